@@ -1,0 +1,386 @@
+"""Benchmark: Floquet steps/s of the kicked-Ising BP-TNS evolution, 127-qubit
+heavy-hex (Eagle layout), chi = 64, on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--chi 64] [--prec fp32] [--theta 0.8] [--presteps 7]
+
+One timed step = one application of U(theta_h) (RX on 127 qubits, 144 ZZ gates
+by BP-gauged simple update with the FP64 truncation solve, BP regauge to the
+tolerance).  The state is evolved `presteps` untimed steps first so that every
+bond has reached chi (steps >= log2(chi) + 1), then W warm-up steps, then K
+timed steps bracketed by CUDA events on the library's stream.
+
+Multi-GPU (torchrun): the theta sweep shards with no collective on the data
+path: rank r evolves its own instance at theta_r from 16 uniform values in
+[0, pi/2]; a barrier and an all-reduce of the elapsed time give max-over-ranks
+timing ("scaling": "weak").
+
+--impl reference times the CPU FP64 oracle (test infrastructure) on bounded
+samples of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Floquet steps/s (127q heavy-hex, chi=64)"
+UNIT = "steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+CSRC = os.path.join(ROOT, "paper_2306_14887_gb300", "csrc")
+
+# nominal figures (GB300): 152 SMs, 128 FP32 lanes per SM, 2070 MHz max clock
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_TFLOPS = 1.25
+TF32_OVER_BF16 = 1.1 / 2.25
+
+# which source file holds the kernels of each profile class
+CLASS_SOURCE = {"bp_contract": "kernels.cu", "gate_env": "kernels.cu", "gate_rebuild": "kernels.cu",
+                "bp_normalise": "kernels.cu", "copyback": "kernels.cu", "phys_gate": "kernels.cu",
+                "rho": "kernels.cu", "trunc_solve": "solve.cu"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--chi", type=int, default=64)
+    p.add_argument("--prec", default="fp32")
+    p.add_argument("--theta", type=float, default=None)
+    p.add_argument("--presteps", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def theta_for(rank, args):
+    if args.theta is not None:
+        return args.theta
+    grid = np.linspace(0.0, np.pi / 2, 16)
+    # interior values: the endpoints are the trivial Clifford points
+    return float(grid[(9 + rank) % 15 or 9])
+
+
+def eagle():
+    import paper_2306_14887_gb300 as tn
+    return tn.heavy_hex(7, 15)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- roofline
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+def src_hash(name):
+    h = hashlib.sha256()
+    h.update(open(os.path.join(CSRC, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(cls):
+    """DRAM bytes per launch of the class from the committed ncu summary, or
+    None when the kernel source changed since the counters were taken."""
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None
+    ent = t.get(cls)
+    if not ent or ent.get("source_sha") != src_hash(CLASS_SOURCE[cls]):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def roofline(prof, prec):
+    cls = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[cls]
+    n = max(1, p["launches"])
+    ms_per = p["ms"] / n
+    pk = peaks()
+    if cls == "trunc_solve":
+        bound, unit, peak = "alu", "TFLOP/s", FP64_TFLOPS
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
+        note = "FP64 ALU, nominal 1.25 TFLOP/s"
+    elif cls in ("bp_contract", "gate_env", "gate_rebuild"):
+        if prec == "fp32":
+            bound, unit, peak = "alu", "TFLOP/s", FP32_SIMT_TFLOPS
+            note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        else:
+            bound, unit = "tensor", "TFLOP/s"
+            peak = pk.get("bf16_tflops", 1900.0) * TF32_OVER_BF16
+            note = "tf32 = measured bf16 burst x nominal tf32/bf16 ratio"
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
+    else:
+        bound, unit, peak = "hbm", "GB/s", pk.get("hbm_gbs", 6792.1)
+        achieved = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+        note = "measured HBM copy"
+    tr = traffic_for(cls)
+    return {"bound": bound, "kernel": cls, "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": unit, "frac": round(achieved / peak, 4),
+            "traffic": tr, "launches": p["launches"], "ms_per_launch": round(ms_per, 4),
+            "share_of_timed": None, "peak_source": note + (" (of measured)" if bound in ("hbm", "tensor") else " (nominal)")}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def oracle_step_estimate(chi, bp_iters, n_gate_sample=6, seed=3):
+    """Time the FP64 oracle on a bounded sample of the 127-qubit chi workload:
+    one synchronous BP sweep and `n_gate_sample` simple-update gates on a random
+    state with every bond at chi; returns (seconds per Floquet step, detail)."""
+    from oracle import bptn as OB
+    from oracle import graph as OG
+    from workloads import random_state
+    g = OG.eagle127()
+    tensors, msgs = random_state([g.degree(v) for v in range(g.n)], g.edges, chi, seed)
+    st = OB.BPState(g, chi)
+    st.T, st.M = tensors, msgs
+    t0 = time.perf_counter()
+    st.bp_sweep()
+    t_sweep = time.perf_counter() - t0
+    order = [e for layer in g.layers() for e in layer]
+    pick = [order[i] for i in np.linspace(0, len(order) - 1, n_gate_sample).astype(int)]
+    t0 = time.perf_counter()
+    for e in pick:
+        st.apply_zz(e)
+    t_gate = (time.perf_counter() - t0) / len(pick)
+    per_step = t_gate * len(g.edges) + bp_iters * t_sweep
+    return per_step, {"t_sweep_s": t_sweep, "t_gate_s": t_gate, "gates_sampled": len(pick)}
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2306_14887_gb300 as tn
+    from paper_2306_14887_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        build.build()
+    else:
+        torch.cuda.set_device(local)
+    chi = args.chi
+    presteps = args.presteps if args.presteps is not None else int(np.log2(max(chi, 1))) + 1
+    theta = theta_for(rank, args)
+    n, edges, cols = eagle()
+    stream = torch.cuda.Stream()
+    s = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream)
+    s.apply_floquet(theta, presteps)
+    for _ in range(args.warmup):
+        s.apply_floquet(theta, 1)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    s.profile_enable(True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    bp_iters = 0
+    disc = 0.0
+    for _ in range(args.steps):
+        s.apply_floquet(theta, 1)
+        st = s.stats()
+        launches += st["kernel_launches"]
+        bp_iters += st["bp_iters_total"]
+        disc = max(disc, st["discarded_max"])
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.profile_enable(False)
+    clocks = clk.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    z = s.expect_z_all()
+    s.close()
+    value = world * args.steps / (ms * 1e-3)
+
+    # end to end through the C ABI: a fresh job from the host graph, each step
+    # followed by the device->host read of <Z_v> for all 127 qubits
+    e2e = None
+    if not args.no_e2e:
+        stream.synchronize()
+        t0 = time.perf_counter()
+        s2 = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream)
+        zs = []
+        for _ in range(args.steps):
+            s2.apply_floquet(theta, 1)
+            zs.append(s2.expect_z_all())
+        s2.close()
+        stream.synchronize()
+        el = time.perf_counter() - t0
+        h2d = edges.nbytes + cols.nbytes
+        e2e = {"value": round(world * args.steps / el, 4), "unit": UNIT,
+               "h2d_bytes_per_step": round(h2d / args.steps, 1),
+               "d2h_bytes_per_step": 8 * n,
+               "note": "fresh job per run: tn_create from the host graph, then per step "
+                       "tn_apply_floquet + tn_expect_z_all (theta passed by value)"}
+    total_ms = sum(v["ms"] for v in prof.values())
+    rl = roofline(prof, args.prec)
+    rl["share_of_timed"] = round(prof[rl["kernel"]]["ms"] / ms, 4)
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32"}.get(args.prec, args.prec) + "+f64solve",
+        "data": "synthetic (initial state |0..0>, theta_h from the uniform [0, pi/2] grid)",
+        "config": {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, "
+                               f"theta_h={theta:.4f}, saturated after {presteps} steps",
+                   "qubits": int(n), "edges": int(len(edges)), "chi": chi,
+                   "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
+                       (36 * 4 * chi ** 3 + 89 * 4 * chi ** 2 + 2 * 4 * chi) * 4 / 1e6),
+                   "parallelism": f"theta-sharded x{world}" if world > 1 else "single GPU"},
+        "gpu_launches": int(launches),
+        "bp_sweeps_per_step": round(bp_iters / args.steps, 2),
+        "discarded_weight_max": disc,
+        "roofline": rl,
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+        "clocks": clocks,
+        "e2e": e2e,
+        "z_mean": float(np.mean(z)),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, det = oracle_step_estimate(chi, bp_iters / args.steps)
+        out["cpu_baseline"] = {"value": round(1.0 / sec, 6), "unit": UNIT, "cores": blas_threads(),
+                               "kind": "oracle",
+                               "sample": "FP64 NumPy oracle on the 127-qubit chi=%d workload: one BP "
+                                         "sweep and %d simple-update gates on a random full-chi "
+                                         "state, scaled to 144 gates + %.1f sweeps per step "
+                                         "(sweep %.2f s, gate %.2f s)" % (
+                                             chi, det["gates_sampled"], bp_iters / args.steps,
+                                             det["t_sweep_s"], det["t_gate_s"])}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    chi = args.chi
+    bp = 4.0  # sweeps per step used to scale the sample (the GPU arm reports its own)
+    times = []
+    for i in range(args.warmup + args.steps):
+        sec, det = oracle_step_estimate(chi, bp, n_gate_sample=2, seed=100 + i)
+        if i >= args.warmup:
+            times.append(sec)
+    per = float(np.mean(times))
+    val = 1.0 / per
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(per * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"eagle127 heavy-hex, chi={chi}, FP64 CPU oracle"},
+           "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": blas_threads(),
+                            "kind": "oracle",
+                            "sample": "each step: one BP sweep + 2 simple-update gates on a random "
+                                      "full-chi 127-qubit state, scaled to 144 gates + %.0f sweeps" % bp},
+           "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

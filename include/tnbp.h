@@ -1,0 +1,274 @@
+/*
+ * tnbp.h — C ABI of the GB300 library for BP-approximated tensor-network
+ * simulation of the kicked-Ising Floquet circuit on heavy-hex lattices
+ * (Tindall, Fishman, Stoudenmire, Sels, arXiv:2306.14887).
+ *
+ * The library evolves |psi(theta_h, n)> = U(theta_h)^n |0...0> (Eq. 1 and
+ * Eq. "State") as a tensor network with one site tensor T_v[p, l_1..l_d] per
+ * qubit (physical index p, one virtual leg of dimension chi per incident edge,
+ * Fig. "heavyhexdiagram"), kept in an arbitrary gauge together with the
+ * belief-propagation (BP) messages of its norm network (Methods, "Belief
+ * propagation on a tensor network state").  One Floquet step is: RX(theta_h)
+ * on every qubit (exact), then exp(+i pi/4 Z_v Z_w) on every edge by the
+ * BP-gauged simple update with truncation back to chi (Methods, "The simple
+ * update procedure"), edge colour layer by layer, then BP regauging.
+ * Expectation values are read from the converged messages (Methods,
+ * "Measuring expectation values within the Vidal gauge").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns tn_status: TN_OK (0) or a negative error code.
+ *   Nothing throws across the ABI and nothing aborts the process.
+ *   tn_last_error() returns a message for the calling thread's last error;
+ *   the string is owned by the library and valid until the next call on
+ *   that thread.
+ * - Host arrays passed in are owned by the caller and copied during the call.
+ *   Host output arrays are owned by the caller and must have the stated size.
+ * - Device memory is obtained through the tn_allocator callbacks given to
+ *   tn_create (NULL: the library calls cudaMalloc/cudaFree itself) and all
+ *   device work runs on the CUDA stream given to tn_create (NULL: the legacy
+ *   default stream).  Calls return after the work they describe has finished
+ *   unless stated otherwise.
+ * - One handle must not be used by two host threads at the same time.
+ * - The device must be an sm_103a GPU (GB300); tn_create fails with
+ *   TN_ECUDA otherwise.
+ */
+#ifndef TNBP_H
+#define TNBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tn_status;
+#define TN_OK 0
+#define TN_EINVAL (-1)         /* bad argument: graph, chi, pointer, size */
+#define TN_ENOMEM (-2)         /* allocation failed or footprint over budget */
+#define TN_ENOTCONVERGED (-3)  /* BP hit max_iters; results are still written */
+#define TN_ENUMERIC (-4)       /* NaN/Inf or a zero-norm message was detected */
+#define TN_ETIMEOUT (-5)       /* a device-side wait gave up */
+#define TN_ECUDA (-6)          /* a CUDA runtime call failed */
+#define TN_EAGAIN (-7)         /* (server) the job is still running */
+#define TN_EUNSUPPORTED (-8)   /* valid request the library does not handle */
+
+typedef struct tn_handle tn_handle;
+
+/*
+ * Interaction graph.  Vertices are qubits 0..n_vertices-1; edges[2e], edges[2e+1]
+ * are the endpoints of edge e.  Every vertex must have degree 1, 2 or 3 and no
+ * edge may repeat or be a self-loop (TN_EINVAL otherwise).  The legs of vertex v
+ * are its incident edges in increasing edge id; site tensors are indexed
+ * T_v[p, leg_0, .., leg_{d-1}] with leg_{d-1} fastest.
+ * colour: n_edges proper edge colours (no two edges at one vertex share a
+ * colour); the ZZ gates are applied colour layer by colour layer in increasing
+ * colour.  NULL lets the library colour the graph (first-fit).
+ * periodic: informational flag (1 when the graph is a periodic unit cell whose
+ * BP fixed point stands for an infinite lattice).
+ */
+typedef struct {
+  int32_t n_vertices;
+  int32_t n_edges;
+  const int32_t* edges;
+  const uint8_t* colour;
+  int32_t periodic;
+} tn_graph;
+
+/* Arithmetic of the message and gate contractions.  FP64 is used for the
+ * truncation solve and for the BP convergence and normalisation reductions
+ * in every mode.  TN_FP32: plain FP32 on the CUDA cores. */
+typedef enum {
+  TN_FP32 = 0,
+  TN_TF32 = 1,
+  TN_BF16 = 2,
+  TN_BF16X3 = 3,
+  TN_TF32X3 = 4
+} tn_precision;
+
+typedef struct {
+  int32_t chi;          /* maximum bond dimension, 1..256 */
+  int32_t prec;         /* tn_precision */
+  double bp_tol;        /* BP stops when max_e ||M_new - M_old||_F < bp_tol */
+  int32_t bp_max_iters; /* BP sweep cap per regauge */
+  double svd_cutoff;    /* singular values below svd_cutoff * sigma_1 are dropped;
+                           <= 0 selects the precision's default */
+  uint64_t seed;        /* reserved (the method draws no random numbers) */
+} tn_config;
+
+/* Device allocator callbacks.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx, void* stream);
+  void (*free)(void* ptr, size_t bytes, void* ctx, void* stream);
+  void* ctx;
+} tn_allocator;
+
+/* Counters of the last tn_apply_floquet / tn_bp_converge call. */
+typedef struct {
+  int32_t steps_done;
+  int32_t bp_iters_last;     /* sweeps of the last regauge */
+  int32_t bp_iters_total;    /* sweeps summed over the call */
+  double bp_residual_last;   /* residual at the end of the last regauge */
+  double discarded_max;      /* largest discarded weight sum(sigma^2 dropped)/sum(sigma^2) */
+  double discarded_sum;      /* summed over all gates of the call */
+  int64_t kernel_launches;   /* device kernels launched by the call */
+} tn_stats;
+
+/*
+ * tn_create — build the state |0...0> (Eq. "State": all spins up) on `graph`
+ * with bond dimension cap cfg->chi: T_v[0, 0..0] = 1, every other entry 0, and
+ * every message the chi x chi matrix with a single 1 at [0, 0] (the exact BP
+ * fixed point of a product state).  *out receives the handle.
+ * Errors: TN_EINVAL (graph or config), TN_ENOMEM, TN_ECUDA.
+ */
+tn_status tn_create(const tn_graph* graph, const tn_config* cfg,
+                    const tn_allocator* alloc, void* cuda_stream, tn_handle** out);
+
+/* tn_destroy — release every device and host resource of the handle. */
+tn_status tn_destroy(tn_handle* h);
+
+/*
+ * tn_apply_floquet — apply U(theta_h) `steps` times (Eq. 1): per step RX(theta_h)
+ * = exp(-i theta_h X/2) on every site, then exp(+i pi/4 Z_v Z_w) on every edge
+ * by the BP-gauged simple update (Methods, "The simple update procedure": the
+ * environment of each tensor is the product of its incoming messages; the
+ * two-site bond is truncated to the chi largest singular values by an FP64
+ * solve; the messages on the gate edge become diag(S) with ||S||_2 = 1), colour
+ * layer by colour layer, then BP regauging with the handle's bp_tol and
+ * bp_max_iters ("State ansatz": regauge after every Trotter step).
+ * theta_h may be any real.  steps >= 0.
+ * Errors: TN_EINVAL, TN_ENUMERIC, TN_ENOTCONVERGED (a regauge hit its cap; the
+ * evolution still completed), TN_ECUDA.
+ */
+tn_status tn_apply_floquet(tn_handle* h, double theta_h, int32_t steps);
+
+/*
+ * tn_apply_clifford_dagger — apply U(pi/2)^dagger `steps` times: the ZZ layers
+ * with exp(-i pi/4 Z_v Z_w), then RX(-pi/2), then BP regauging.  This is the
+ * "extended time evolution" used to measure the Pauli string
+ * U^n'(pi/2) Z_i U^n'(pi/2)^dagger as <Z_i> ("Measuring expectation values").
+ */
+tn_status tn_apply_clifford_dagger(tn_handle* h, int32_t steps);
+
+/*
+ * tn_bp_converge — iterate the BP equations (Eq. "MessageTensorSelfConsistency")
+ * with a synchronous schedule from the current messages: every directed message
+ * M_{v->w}[e, e'] = sum T_v[p, .., e, ..] conj(T_v[p, .., e', ..]) prod_{x != w}
+ * M_{x->v}, then Hermitised and scaled to unit Frobenius norm.  Stops when
+ * max_e ||M_new - M_old||_F < tol (FP64 reduction) or after max_iters sweeps.
+ * iters_out / residual_out may be NULL.
+ * Errors: TN_ENOTCONVERGED (cap reached), TN_ENUMERIC, TN_EINVAL, TN_ECUDA.
+ */
+tn_status tn_bp_converge(tn_handle* h, double tol, int32_t max_iters,
+                         int32_t* iters_out, double* residual_out);
+
+/* A Pauli string sign * prod_j P_{sites[j]}, P in {'X','Y','Z'}; sites distinct. */
+typedef struct {
+  int32_t weight;
+  const int32_t* sites;
+  const char* paulis;
+  int8_t sign;
+} tn_pauli;
+
+/*
+ * tn_expect — expectation values of n_ops Pauli strings from the current
+ * state and messages (Methods, "Measuring expectation values within the Vidal
+ * gauge": the environment of a region is the product of its incoming BP
+ * messages).  Weight-1 strings use rho_v[p, p'] = sum T_v[p, ..] conj(T_v[p', ..])
+ * prod_x M_{x->v} and <P> = Tr(rho P) / Tr(rho).
+ * method 0: strings of weight > 1 are contracted exactly over a tree spanning
+ *           their support, every other edge closed by the converged messages.
+ * method 1: "extended time evolution": the library finds (i, n') with
+ *           string = +-U^n'(pi/2) Z_i U^n'(pi/2)^dagger by Pauli propagation, evolves
+ *           a copy of the state by U(pi/2)^dagger n' times and measures Z_i;
+ *           TN_EUNSUPPORTED if no n' <= 32 reduces the string to one Z.
+ * out: n_ops doubles (real parts; Pauli strings are Hermitian).
+ */
+tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t method,
+                    double* out);
+
+/*
+ * tn_clifford_reduce — host-only: find n' <= max_steps and a site i with
+ * op = sign * U^n'(pi/2) Z_i U^n'(pi/2)^dagger ("Measuring expectation values":
+ * any such string is one Z conjugated by the Clifford circuit U(pi/2)), by
+ * propagating op through U(pi/2)^dagger.  sign_out includes op->sign.
+ * Errors: TN_EINVAL (graph or string), TN_EUNSUPPORTED (no such n').
+ */
+tn_status tn_clifford_reduce(const tn_graph* graph, const tn_pauli* op, int32_t max_steps,
+                             int32_t* site_out, int32_t* nprime_out, int32_t* sign_out);
+
+/* tn_expect_z_all — <Z_v> for every vertex v (out: n_vertices doubles). */
+tn_status tn_expect_z_all(tn_handle* h, double* out);
+
+/* tn_get_stats — counters of the last evolution call. */
+tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
+
+/*
+ * State transfer (tests, checkpoint/resume).  Site tensors cross the ABI as
+ * interleaved complex64 (re, im) with shape (2, chi, .., chi) in leg order
+ * (2 * chi^d complex values); messages as chi x chi complex64 row-major
+ * [ket, bra].  The message from `src` across edge e is selected by (e, src).
+ */
+tn_status tn_get_site(tn_handle* h, int32_t v, float* host_out, size_t n_floats);
+tn_status tn_set_site(tn_handle* h, int32_t v, const float* host_in, size_t n_floats);
+tn_status tn_get_message(tn_handle* h, int32_t e, int32_t src, float* host_out,
+                         size_t n_floats);
+tn_status tn_set_message(tn_handle* h, int32_t e, int32_t src, const float* host_in,
+                         size_t n_floats);
+/* Bytes of device memory the handle holds (state, messages, workspaces). */
+tn_status tn_footprint(const tn_handle* h, size_t* bytes_out);
+/* Footprint tn_create would need for this graph and config (admission). */
+tn_status tn_footprint_estimate(const tn_graph* graph, const tn_config* cfg,
+                                size_t* bytes_out);
+
+/*
+ * tn_heavy_hex — the heavy-hex patch with `rows` rows (odd) of `cols` columns
+ * (cols = 3 mod 4): row 0 has no last column, the last row no first column;
+ * between rows r and r+1 a bridge qubit sits at columns = 0 mod 4 (r even) or
+ * 2 mod 4 (r odd); numbering row-major with each bridge row after the row above
+ * (Fig. "heavyhexdiagram"; (7, 15) is the 127-qubit Eagle layout with the
+ * dangling qubits 13 and 113).  Edges are sorted by (min, max) endpoint.
+ * Colours: row edge (r,c)-(r,c+1) gets [0,1,2,1][c%4] on even r and
+ * [1,0,1,2][c%4] on odd r; a bridge's upper edge 2 and its lower edge 0.
+ * edges_out holds 2*capacity ints, colours_out capacity bytes (either may be
+ * NULL to query sizes).  TN_EINVAL if the shape is invalid or capacity short.
+ */
+tn_status tn_heavy_hex(int32_t rows, int32_t cols, int32_t* n_vertices, int32_t* n_edges,
+                       int32_t* edges_out, uint8_t* colours_out, int32_t capacity);
+
+/*
+ * Per-kernel-class timing.  While enabled, every kernel the handle launches is
+ * bracketed by CUDA events on the handle's stream and its algorithmic work is
+ * added to its class: flops = 8 per complex multiply-add of the contraction
+ * (40 (2 chi)^3 per edge for the FP64 truncation solve), bytes = every operand
+ * element read once and every result written once.  Classes (index: name):
+ * 0 bp_contract, 1 bp_normalise, 2 gate_env, 3 trunc_solve, 4 gate_rebuild,
+ * 5 copyback, 6 phys_gate, 7 rho.
+ */
+typedef struct {
+  int32_t n_classes;
+  int64_t launches[16];
+  double ms[16];
+  double flops[16];
+  double bytes[16];
+} tn_profile;
+/* tn_profile_enable — switch timing on (1) or off (0); resets the counters. */
+tn_status tn_profile_enable(tn_handle* h, int32_t on);
+/* tn_profile_read — synchronise the handle's stream and copy the counters. */
+tn_status tn_profile_read(tn_handle* h, tn_profile* out);
+/* tn_profile_class_name — name of class cls ("" when out of range), static storage. */
+const char* tn_profile_class_name(int32_t cls);
+
+/* tn_last_error — message of the calling thread's last failed call ("" if none). */
+const char* tn_last_error(void);
+
+/* tn_version — library version string, static storage. */
+const char* tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNBP_H */

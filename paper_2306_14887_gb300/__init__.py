@@ -1,0 +1,345 @@
+"""Python binding of the tnbp C ABI (include/tnbp.h): argument marshalling only.
+
+Every step of the simulation runs in the CUDA library ``libtnbp.so`` built
+in-tree for sm_103a; this module loads it with ctypes, passes plain pointers
+and sizes, and binds the library's device allocator to PyTorch's caching
+allocator.  There is no CPU fallback: if the library is missing or cannot
+load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtnbp.so")
+
+TN_OK = 0
+STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ENOTCONVERGED",
+          -4: "TN_ENUMERIC", -5: "TN_ETIMEOUT", -6: "TN_ECUDA", -7: "TN_EAGAIN",
+          -8: "TN_EUNSUPPORTED"}
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
+
+#: every symbol include/tnbp.h declares
+EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dagger",
+           "tn_bp_converge", "tn_expect", "tn_expect_z_all", "tn_get_stats", "tn_get_site",
+           "tn_set_site", "tn_get_message", "tn_set_message", "tn_footprint",
+           "tn_footprint_estimate", "tn_heavy_hex", "tn_clifford_reduce", "tn_profile_enable",
+           "tn_profile_read", "tn_profile_class_name", "tn_last_error", "tn_version"]
+
+
+class TNError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tn_graph(C.Structure):
+    _fields_ = [("n_vertices", C.c_int32), ("n_edges", C.c_int32),
+                ("edges", C.POINTER(C.c_int32)), ("colour", C.POINTER(C.c_uint8)),
+                ("periodic", C.c_int32)]
+
+
+class tn_config(C.Structure):
+    _fields_ = [("chi", C.c_int32), ("prec", C.c_int32), ("bp_tol", C.c_double),
+                ("bp_max_iters", C.c_int32), ("svd_cutoff", C.c_double), ("seed", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class tn_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class tn_stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int32), ("bp_iters_last", C.c_int32),
+                ("bp_iters_total", C.c_int32), ("bp_residual_last", C.c_double),
+                ("discarded_max", C.c_double), ("discarded_sum", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+class tn_profile(C.Structure):
+    _fields_ = [("n_classes", C.c_int32), ("launches", C.c_int64 * 16), ("ms", C.c_double * 16),
+                ("flops", C.c_double * 16), ("bytes", C.c_double * 16)]
+
+
+class tn_pauli(C.Structure):
+    _fields_ = [("weight", C.c_int32), ("sites", C.POINTER(C.c_int32)),
+                ("paulis", C.c_char_p), ("sign", C.c_int8)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtnbp.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing; run paper_2306_14887_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, dp = C.c_void_p, C.c_int32, C.POINTER(C.c_double)
+        L.tn_create.argtypes = [C.POINTER(tn_graph), C.POINTER(tn_config),
+                                C.POINTER(tn_allocator), vp, C.POINTER(vp)]
+        L.tn_destroy.argtypes = [vp]
+        L.tn_apply_floquet.argtypes = [vp, C.c_double, i32]
+        L.tn_apply_clifford_dagger.argtypes = [vp, i32]
+        L.tn_bp_converge.argtypes = [vp, C.c_double, i32, C.POINTER(i32), dp]
+        L.tn_expect.argtypes = [vp, C.POINTER(tn_pauli), i32, i32, dp]
+        L.tn_expect_z_all.argtypes = [vp, dp]
+        L.tn_get_stats.argtypes = [vp, C.POINTER(tn_stats)]
+        fp = C.POINTER(C.c_float)
+        L.tn_get_site.argtypes = [vp, i32, fp, C.c_size_t]
+        L.tn_set_site.argtypes = [vp, i32, fp, C.c_size_t]
+        L.tn_get_message.argtypes = [vp, i32, i32, fp, C.c_size_t]
+        L.tn_set_message.argtypes = [vp, i32, i32, fp, C.c_size_t]
+        L.tn_footprint.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.tn_footprint_estimate.argtypes = [C.POINTER(tn_graph), C.POINTER(tn_config),
+                                            C.POINTER(C.c_size_t)]
+        L.tn_heavy_hex.argtypes = [i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                   C.POINTER(C.c_uint8), i32]
+        L.tn_clifford_reduce.argtypes = [C.POINTER(tn_graph), C.POINTER(tn_pauli), i32,
+                                         C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.tn_profile_enable.argtypes = [vp, i32]
+        L.tn_profile_read.argtypes = [vp, C.POINTER(tn_profile)]
+        L.tn_profile_class_name.argtypes = [i32]
+        L.tn_profile_class_name.restype = C.c_char_p
+        L.tn_last_error.restype = C.c_char_p
+        L.tn_version.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("tn_last_error", "tn_version", "tn_profile_class_name"):
+                getattr(L, name).restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != TN_OK:
+        raise TNError(status, lib().tn_last_error().decode())
+    return status
+
+
+def heavy_hex(rows, cols):
+    """(n_vertices, edges [m, 2] int32, colours [m] uint8) from the library's generator."""
+    L = lib()
+    n, m = C.c_int32(), C.c_int32()
+    _check(L.tn_heavy_hex(rows, cols, C.byref(n), C.byref(m), None, None, 0))
+    edges = np.zeros((m.value, 2), dtype=np.int32)
+    cols_ = np.zeros(m.value, dtype=np.uint8)
+    _check(L.tn_heavy_hex(rows, cols, C.byref(n), C.byref(m),
+                          edges.ctypes.data_as(C.POINTER(C.c_int32)),
+                          cols_.ctypes.data_as(C.POINTER(C.c_uint8)), m.value))
+    return n.value, edges, cols_
+
+
+def clifford_reduce(n, edges, ops, sign=1, max_steps=32, colours=None):
+    """(site, n', sign) with ops = sign * U^n'(pi/2) Z_site U^n'(pi/2)^dagger (host-only)."""
+    g, _keep = _graph_struct(n, edges, colours)
+    sites = np.array(sorted(ops), dtype=np.int32)
+    labels = "".join(ops[int(q)] for q in sites).encode()
+    p = tn_pauli(len(sites), sites.ctypes.data_as(C.POINTER(C.c_int32)), labels, int(sign))
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().tn_clifford_reduce(C.byref(g), C.byref(p), int(max_steps), C.byref(a),
+                                    C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def _graph_struct(n, edges, colours):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    g = tn_graph()
+    g.n_vertices = int(n)
+    g.n_edges = len(e) // 2
+    g.edges = e.ctypes.data_as(C.POINTER(C.c_int32))
+    keep = [e]
+    if colours is not None:
+        c = np.ascontiguousarray(np.asarray(colours, dtype=np.uint8))
+        g.colour = c.ctypes.data_as(C.POINTER(C.c_uint8))
+        keep.append(c)
+    else:
+        g.colour = C.POINTER(C.c_uint8)()
+    g.periodic = 0
+    return g, keep
+
+
+def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff):
+    c = tn_config()
+    c.chi = int(chi)
+    c.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    c.bp_tol = float(bp_tol)
+    c.bp_max_iters = int(bp_max_iters)
+    c.svd_cutoff = float(svd_cutoff)
+    c.seed = 0
+    return c
+
+
+def footprint_estimate(n, edges, colours, chi, prec="fp32"):
+    g, _keep = _graph_struct(n, edges, colours)
+    cfg = _config(chi, prec, 1e-10, 1, 0.0)
+    out = C.c_size_t()
+    _check(lib().tn_footprint_estimate(C.byref(g), C.byref(cfg), C.byref(out)))
+    return out.value
+
+
+class TNState:
+    """A tensor-network state on one graph, resident on the current CUDA device."""
+
+    def __init__(self, n, edges, colours=None, chi=8, prec="fp32", bp_tol=1e-10,
+                 bp_max_iters=1000, svd_cutoff=0.0, stream=None, torch_allocator=True):
+        import torch
+        self._torch = torch
+        L = lib()
+        self.n = int(n)
+        self.edges = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+        self.chi = int(chi)
+        g, self._keep = _graph_struct(n, edges, colours)
+        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self._sp = sp
+        self._alloc = None
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+
+            def _a(size, ctx, st):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), dev, int(st or 0))
+                except Exception:
+                    return None
+
+            def _f(ptr, size, ctx, st):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._cb = (ALLOC_FN(_a), FREE_FN(_f))
+            self._alloc = tn_allocator(self._cb[0], self._cb[1], None)
+        h = C.c_void_p()
+        _check(L.tn_create(C.byref(g), C.byref(cfg),
+                           C.byref(self._alloc) if self._alloc is not None else None,
+                           C.c_void_p(sp), C.byref(h)))
+        self._h = h
+
+    # ------------------------------------------------------------------ life
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- evolution
+    def apply_floquet(self, theta, steps, check=True):
+        s = lib().tn_apply_floquet(self._h, float(theta), int(steps))
+        if check and s not in (TN_OK, -3):
+            _check(s)
+        return s
+
+    def apply_clifford_dagger(self, steps):
+        s = lib().tn_apply_clifford_dagger(self._h, int(steps))
+        if s not in (TN_OK, -3):
+            _check(s)
+        return s
+
+    def bp_converge(self, tol=1e-10, max_iters=1000):
+        it, res = C.c_int32(), C.c_double()
+        s = lib().tn_bp_converge(self._h, float(tol), int(max_iters), C.byref(it), C.byref(res))
+        if s not in (TN_OK, -3):
+            _check(s)
+        return it.value, res.value, s
+
+    # ---------------------------------------------------------- expectations
+    def expect_z_all(self):
+        out = np.zeros(self.n, dtype=np.float64)
+        _check(lib().tn_expect_z_all(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def expect(self, strings, method=1):
+        """strings: list of (dict {site: 'X'|'Y'|'Z'}, sign)."""
+        arr = (tn_pauli * len(strings))()
+        keep = []
+        for i, (ops, sign) in enumerate(strings):
+            sites = np.array(sorted(ops), dtype=np.int32)
+            labels = "".join(ops[int(q)] for q in sites).encode()
+            keep.append((sites, labels))
+            arr[i].weight = len(sites)
+            arr[i].sites = sites.ctypes.data_as(C.POINTER(C.c_int32))
+            arr[i].paulis = labels
+            arr[i].sign = int(sign)
+        out = np.zeros(len(strings), dtype=np.float64)
+        _check(lib().tn_expect(self._h, arr, len(strings), int(method),
+                               out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def stats(self):
+        s = tn_stats()
+        _check(lib().tn_get_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in tn_stats._fields_}
+
+    def profile_enable(self, on=True):
+        _check(lib().tn_profile_enable(self._h, 1 if on else 0))
+
+    def profile(self):
+        """{class name: {launches, ms, flops, bytes}} since profile_enable."""
+        p = tn_profile()
+        _check(lib().tn_profile_read(self._h, C.byref(p)))
+        out = {}
+        for c in range(p.n_classes):
+            name = lib().tn_profile_class_name(c).decode()
+            out[name] = {"launches": p.launches[c], "ms": p.ms[c], "flops": p.flops[c],
+                         "bytes": p.bytes[c]}
+        return out
+
+    def footprint(self):
+        out = C.c_size_t()
+        _check(lib().tn_footprint(self._h, C.byref(out)))
+        return out.value
+
+    # ------------------------------------------------------------ state I/O
+    def degree(self, v):
+        return int(np.sum(self.edges == v))
+
+    def get_site(self, v):
+        d = self.degree(v)
+        buf = np.zeros(4 * self.chi ** d, dtype=np.float32)
+        _check(lib().tn_get_site(self._h, int(v), buf.ctypes.data_as(C.POINTER(C.c_float)),
+                                 buf.size))
+        z = buf[0::2] + 1j * buf[1::2]
+        return z.reshape((2,) + (self.chi,) * d)
+
+    def set_site(self, v, t):
+        t = np.asarray(t, dtype=np.complex64).reshape(-1)
+        buf = np.empty(2 * t.size, dtype=np.float32)
+        buf[0::2], buf[1::2] = t.real, t.imag
+        _check(lib().tn_set_site(self._h, int(v), buf.ctypes.data_as(C.POINTER(C.c_float)),
+                                 buf.size))
+
+    def get_message(self, e, src):
+        buf = np.zeros(2 * self.chi ** 2, dtype=np.float32)
+        _check(lib().tn_get_message(self._h, int(e), int(src),
+                                    buf.ctypes.data_as(C.POINTER(C.c_float)), buf.size))
+        return (buf[0::2] + 1j * buf[1::2]).reshape(self.chi, self.chi)
+
+    def set_message(self, e, src, m):
+        m = np.asarray(m, dtype=np.complex64).reshape(-1)
+        buf = np.empty(2 * m.size, dtype=np.float32)
+        buf[0::2], buf[1::2] = m.real, m.imag
+        _check(lib().tn_set_message(self._h, int(e), int(src),
+                                    buf.ctypes.data_as(C.POINTER(C.c_float)), buf.size))
+
+
+def version():
+    return lib().tn_version().decode()

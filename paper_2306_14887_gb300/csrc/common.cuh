@@ -1,0 +1,100 @@
+// Shared definitions of the tnbp CUDA library (internal; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tnbp.h"
+
+namespace tnbp {
+
+// Thread-local error message behind tn_last_error().
+void set_error(const std::string& msg);
+
+#define TN_CUDA_TRY(expr)                                                        \
+  do {                                                                          \
+    cudaError_t err__ = (expr);                                                 \
+    if (err__ != cudaSuccess) {                                                 \
+      ::tnbp::set_error(std::string(#expr) + ": " + cudaGetErrorString(err__)); \
+      return TN_ECUDA;                                                          \
+    }                                                                           \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Batched strided complex GEMM on planar complex FP32 data.
+//
+//   C[m][n] (+)= alpha * sum_k opA(A)[m][k] * opB(B)[k][n]
+//
+// The contraction index k runs over K1 * K2 values, k = k1 * K2 + k2, so that
+// a contraction over two tensor legs with unrelated strides is one GEMM.
+// Element (m, k1, k2) of A is at A + m*a_m + k1*a_k1 + k2*a_k2; likewise B and
+// C.  Each operand is planar: the imaginary plane starts plane_* floats after
+// the real plane.  The batch is outer x inner: the outer index selects base
+// pointers from device arrays, the inner index adds inner * *_in.
+// ---------------------------------------------------------------------------
+struct GemmDesc {
+  const float* const* A;
+  const float* const* B;
+  float* const* C;
+  int64_t plane_a, plane_b, plane_c;
+  int32_t M, N, K1, K2;
+  int64_t a_m, a_k1, a_k2;
+  int64_t b_k1, b_k2, b_n;
+  int64_t c_m, c_n;
+  int32_t n_outer, n_inner;
+  int64_t a_in, b_in, c_in;
+  int32_t conj_a, conj_b;
+  int32_t accumulate;
+  int32_t prec;  // tn_precision of the contraction
+};
+
+// Launch helpers implemented in kernels.cu / solve.cu.  All return a
+// cudaError_t from the launch.
+cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s);
+
+// RX-type 2x2 on the physical leg: T[p] <- sum_q U[p][q] T[q] for every site in
+// the list.  site_off: float offset of each site's real plane; len: chi^d
+// complex entries per physical value; plane: 2*chi^d.
+cudaError_t launch_phys_gate(float* T, const int64_t* site_off, int n_sites, int64_t len,
+                             int64_t plane, float u00r, float u00i, float u01r, float u01i,
+                             float u10r, float u10i, float u11r, float u11i, cudaStream_t s);
+
+// Hermitise, normalise (Frobenius, FP64) and compare raw messages against the
+// current ones: msg <- normalise(raw); residual <- max ||new - old||_F.
+// res_bits: one unsigned long long holding the max residual as IEEE bits;
+// flags: bit 0 set on a non-finite or zero-norm message.
+cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
+                             unsigned long long* res_bits, int* flags, cudaStream_t s);
+
+// rho[site][p][p'] = sum_r X[p][r] conj(T[p'][r]) in FP64 (complex, 8 doubles
+// per site).  x_off / t_off: real-plane offsets; len = chi^d; plane = 2*len.
+cudaError_t launch_rho(const float* X, const float* T, const int64_t* x_off,
+                       const int64_t* t_off, int n_sites, int64_t len, int64_t plane,
+                       double* rho, cudaStream_t s);
+
+// Batched copy of equally sized blocks: dst[i][0..n) = src[i][0..n).
+cudaError_t launch_copy_blocks(float* const* dst, const float* const* src, int n_blocks,
+                               int64_t n_floats, cudaStream_t s);
+
+// FP64 truncation solve for one colour layer (see solve.cu).
+struct SolveArgs {
+  int n_edges;
+  int chi;
+  int sign;                 // +1: exp(+i pi/4 ZZ); -1: exp(-i pi/4 ZZ)
+  double gram_cut;          // relative eigenvalue cutoff of the v-side Gram
+  double svd_cut;           // relative singular-value cutoff
+  const float* gram;        // [edge][side][p][plane][chi][chi]
+  float* dmat;              // [edge][side][p][plane][chi][chi]
+  float* msg;               // message buffer [2E][plane][chi][chi]
+  const int32_t* msg_vw;    // per edge: directed index of v->w and w->v
+  double* work;             // [edge][6][n][n] complex doubles
+  double* stats;            // per edge: [discarded weight, kept, sigma_1, min_gap]
+  int* flags;
+  int max_sweeps;
+};
+cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s);
+size_t solve_work_doubles(int chi);
+
+}  // namespace tnbp

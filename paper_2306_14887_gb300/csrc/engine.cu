@@ -1,0 +1,1280 @@
+// Engine and C ABI of the tnbp library (declarations in include/tnbp.h).
+//
+// Device state of a handle, all planar complex FP32 unless noted:
+//   T       site tensors, site v at t_off[v]: [re|im][p][leg_0]..[leg_{d-1}]
+//           (each plane 2*chi^d floats, legs padded to chi, increasing edge id)
+//   Ts      rebuild target of the gate layers (same layout as T)
+//   Y1, Y2  intermediates of the leg-by-leg contractions (same layout as T)
+//   msg     canonical BP messages [2E][re|im][chi][chi], index [ket][bra];
+//           directed id 2e + 0: from eu[e] to ew[e]; 2e + 1: from ew[e] to eu[e]
+//   raw     un-normalised messages of the sweep in flight (same layout)
+//   gram    open-p environments of a gate layer [slot][side][p][re|im][chi][chi]
+//   dmat    per-p gate-leg matrices from the FP64 solve (same layout)
+//   work    FP64 solve workspace
+//
+// One Floquet step (Eq. 1): RX on every site, then per colour layer the gate
+// environments (the message contraction with p left open, both sides of every
+// edge of the layer), the FP64 truncation solve, the rebuild of both site
+// tensors, then BP regauging (synchronous sweeps until the FP64 residual is
+// below tol).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "graph.h"
+#include "tnbp.h"
+
+namespace tnbp {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+
+namespace {
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+struct HostLaunch {
+  GemmDesc d;
+  std::vector<const float*> A, B;
+  std::vector<float*> C;
+};
+
+struct Plan {
+  std::vector<HostLaunch> L;
+};
+
+struct CopyLaunch {
+  std::vector<float*> dst;
+  std::vector<const float*> src;
+  int64_t n_floats = 0;
+  float* const* d_dst = nullptr;
+  const float* const* d_src = nullptr;
+};
+
+struct RhoLaunch {
+  int deg = 0;
+  std::vector<int64_t> x_off, t_off;
+  std::vector<int> sites;
+  const int64_t* d_x = nullptr;
+  const int64_t* d_t = nullptr;
+};
+
+}  // namespace
+}  // namespace tnbp
+
+struct tn_handle {
+  tnbp::HostGraph g;
+  tn_config cfg{};
+  int chi = 0;
+  cudaStream_t stream = nullptr;
+  tn_allocator alloc{};
+  bool own_alloc = true;
+  std::vector<std::pair<void*, size_t>> allocations;
+  size_t bytes = 0;
+
+  std::vector<int64_t> t_off;      // per site (floats)
+  std::vector<int64_t> t_len;      // chi^d per site
+  int64_t t_floats = 0;
+  float *T = nullptr, *Ts = nullptr, *Y1 = nullptr, *Y2 = nullptr;
+  float *msg = nullptr, *raw = nullptr, *gram = nullptr, *dmat = nullptr;
+  double* work = nullptr;
+  double* solve_stats = nullptr;
+  int32_t* msg_vw = nullptr;      // per layer slot: directed ids of v->w and w->v
+  std::vector<std::vector<int32_t>> layer_msg_vw;  // host copy per layer
+  std::vector<int32_t*> d_layer_msg_vw;
+  int max_layer = 0;
+  unsigned long long* res_bits = nullptr;
+  int* flags = nullptr;
+  double* rho = nullptr;
+  int64_t* site_offs_by_deg[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_by_deg[4] = {0, 0, 0, 0};
+  std::vector<int> sites_by_deg[4];
+
+  tnbp::Plan sweep;
+  std::vector<tnbp::Plan> gate_env, rebuild;
+  std::vector<std::vector<tnbp::CopyLaunch>> copyback;
+  tnbp::Plan rho_prep;
+  std::vector<tnbp::RhoLaunch> rho_l;
+  void* arena = nullptr;
+
+  // backup for the extended-evolution expectation
+  float *T_bak = nullptr, *msg_bak = nullptr;
+
+  tn_stats stats{};
+  double* h_stats = nullptr;  // host copy of solve stats
+
+  // per-kernel-class timing with CUDA events on the handle's stream
+  bool prof_on = false;
+  struct ProfEv { int cls; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<ProfEv> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  tn_profile prof{};
+};
+
+namespace tnbp {
+namespace {
+
+void* dev_alloc(tn_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->own_alloc) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  } else {
+    p = h->alloc.alloc(bytes, h->alloc.ctx, (void*)h->stream);
+    if (!p) return nullptr;
+  }
+  h->allocations.push_back({p, bytes});
+  h->bytes += bytes;
+  return p;
+}
+
+void dev_free_all(tn_handle* h) {
+  for (auto& a : h->allocations) {
+    if (h->own_alloc) cudaFree(a.first);
+    else h->alloc.free(a.first, a.second, h->alloc.ctx, (void*)h->stream);
+  }
+  h->allocations.clear();
+  h->bytes = 0;
+}
+
+int dir_id(const HostGraph& g, int src, int e) { return 2 * e + (g.eu[e] == src ? 0 : 1); }
+
+// ----------------------------------------------------------------- builders
+GemmDesc blank_desc(int prec) {
+  GemmDesc d;
+  memset(&d, 0, sizeof(d));
+  d.n_outer = 0;
+  d.n_inner = 1;
+  d.K1 = 1;
+  d.prec = prec;
+  return d;
+}
+
+// Y = X x_j M on degree-d tensors (leg j contracted with M's row index, the
+// result keeps M's column index in place of leg j).  entries: (X, M, Y).
+void add_mode_product(Plan& P, int d, int j, int chi, int prec,
+                      const std::vector<std::array<const float*, 3>>& ent) {
+  if (ent.empty()) return;
+  HostLaunch L;
+  L.d = blank_desc(prec);
+  const int64_t inner = ipow(chi, d - 1 - j);
+  const int64_t plane = 2 * ipow(chi, d);
+  const int64_t c2 = (int64_t)chi * chi;
+  if (inner == 1) {  // rows (p, legs before j): Y = X M
+    L.d.M = (int)(2 * ipow(chi, d - 1));
+    L.d.N = chi;
+    L.d.K2 = chi;
+    L.d.a_m = chi; L.d.a_k2 = 1;
+    L.d.b_k2 = chi; L.d.b_n = 1;
+    L.d.c_m = chi; L.d.c_n = 1;
+    L.d.plane_a = plane; L.d.plane_b = c2; L.d.plane_c = plane;
+    for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
+  } else {           // per (p, legs before j): Y[o] = M^T X[o]
+    L.d.M = chi;
+    L.d.N = (int)inner;
+    L.d.K2 = chi;
+    L.d.a_m = 1; L.d.a_k2 = chi;
+    L.d.b_k2 = inner; L.d.b_n = 1;
+    L.d.c_m = inner; L.d.c_n = 1;
+    L.d.n_inner = (int)(2 * ipow(chi, j));
+    L.d.a_in = 0; L.d.b_in = chi * inner; L.d.c_in = chi * inner;
+    L.d.plane_a = c2; L.d.plane_b = plane; L.d.plane_c = plane;
+    for (auto& e : ent) { L.A.push_back(e[1]); L.B.push_back(e[0]); L.C.push_back((float*)e[2]); }
+  }
+  L.d.n_outer = (int)ent.size();
+  P.L.push_back(std::move(L));
+}
+
+// out[e][e'] = sum_{all but leg j} Y[.., e, ..] conj(T[.., e', ..]); with open_p
+// the sum excludes p and two matrices (p = 0, 1) are written 2*chi^2 apart.
+// entries: (Y, T, out).
+void add_close(Plan& P, int d, int j, int chi, bool open_p, int prec,
+               const std::vector<std::array<const float*, 3>>& ent) {
+  if (ent.empty()) return;
+  HostLaunch L;
+  L.d = blank_desc(prec);
+  const int64_t inner = ipow(chi, d - 1 - j);
+  const int64_t outer_legs = ipow(chi, j);
+  const int64_t plane = 2 * ipow(chi, d);
+  const int64_t c2 = (int64_t)chi * chi;
+  L.d.M = chi;
+  L.d.N = chi;
+  L.d.K1 = (int)(open_p ? outer_legs : 2 * outer_legs);
+  L.d.K2 = (int)inner;
+  L.d.a_m = inner; L.d.a_k1 = chi * inner; L.d.a_k2 = 1;
+  L.d.b_k1 = chi * inner; L.d.b_k2 = 1; L.d.b_n = inner;
+  L.d.c_m = chi; L.d.c_n = 1;
+  L.d.conj_b = 1;
+  L.d.plane_a = plane; L.d.plane_b = plane; L.d.plane_c = c2;
+  if (open_p) {
+    L.d.n_inner = 2;
+    L.d.a_in = ipow(chi, d); L.d.b_in = ipow(chi, d); L.d.c_in = 2 * c2;
+  }
+  for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
+  L.d.n_outer = (int)ent.size();
+  P.L.push_back(std::move(L));
+}
+
+// T'[p][.., n, ..] = sum_e T[p][.., e, ..] D_p[e][n] on leg j.  entries: (T_p, D_p, T'_p)
+// with one entry per (site, p).
+void add_leg_matrix(Plan& P, int d, int j, int chi, int prec,
+                    const std::vector<std::array<const float*, 3>>& ent) {
+  if (ent.empty()) return;
+  HostLaunch L;
+  L.d = blank_desc(prec);
+  const int64_t inner = ipow(chi, d - 1 - j);
+  const int64_t plane = 2 * ipow(chi, d);
+  const int64_t c2 = (int64_t)chi * chi;
+  if (inner == 1) {
+    L.d.M = (int)ipow(chi, d - 1);
+    L.d.N = chi;
+    L.d.K2 = chi;
+    L.d.a_m = chi; L.d.a_k2 = 1;
+    L.d.b_k2 = chi; L.d.b_n = 1;
+    L.d.c_m = chi; L.d.c_n = 1;
+    L.d.plane_a = plane; L.d.plane_b = c2; L.d.plane_c = plane;
+    for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
+  } else {
+    L.d.M = chi;
+    L.d.N = (int)inner;
+    L.d.K2 = chi;
+    L.d.a_m = 1; L.d.a_k2 = chi;
+    L.d.b_k2 = inner; L.d.b_n = 1;
+    L.d.c_m = inner; L.d.c_n = 1;
+    L.d.n_inner = (int)ipow(chi, j);
+    L.d.a_in = 0; L.d.b_in = chi * inner; L.d.c_in = chi * inner;
+    L.d.plane_a = c2; L.d.plane_b = plane; L.d.plane_c = plane;
+    for (auto& e : ent) { L.A.push_back(e[1]); L.B.push_back(e[0]); L.C.push_back((float*)e[2]); }
+  }
+  L.d.n_outer = (int)ent.size();
+  P.L.push_back(std::move(L));
+}
+
+tn_status upload_plans(tn_handle* h) {
+  // gather every pointer array into one arena
+  std::vector<const void*> all;
+  std::vector<Plan*> plans = {&h->sweep, &h->rho_prep};
+  for (auto& p : h->gate_env) plans.push_back(&p);
+  for (auto& p : h->rebuild) plans.push_back(&p);
+  size_t count = 0;
+  for (Plan* p : plans)
+    for (auto& L : p->L) count += L.A.size() * 3;
+  for (auto& v : h->copyback)
+    for (auto& c : v) count += c.dst.size() * 2;
+  size_t n64 = 0;
+  for (auto& r : h->rho_l) n64 += r.x_off.size() * 2;
+  const size_t bytes = count * sizeof(void*) + n64 * sizeof(int64_t);
+  void* arena = dev_alloc(h, bytes);
+  if (!arena) {
+    set_error("device allocation of the plan arena failed");
+    return TN_ENOMEM;
+  }
+  h->arena = arena;
+  std::vector<unsigned char> host(bytes);
+  size_t pos = 0;
+  auto put_ptrs = [&](const void* const* src, size_t n) -> void* {
+    void* dev = (unsigned char*)arena + pos;
+    memcpy(host.data() + pos, src, n * sizeof(void*));
+    pos += n * sizeof(void*);
+    return dev;
+  };
+  for (Plan* p : plans)
+    for (auto& L : p->L) {
+      L.d.A = (const float* const*)put_ptrs((const void* const*)L.A.data(), L.A.size());
+      L.d.B = (const float* const*)put_ptrs((const void* const*)L.B.data(), L.B.size());
+      L.d.C = (float* const*)put_ptrs((const void* const*)L.C.data(), L.C.size());
+    }
+  for (auto& v : h->copyback)
+    for (auto& c : v) {
+      c.d_dst = (float* const*)put_ptrs((const void* const*)c.dst.data(), c.dst.size());
+      c.d_src = (const float* const*)put_ptrs((const void* const*)c.src.data(), c.src.size());
+    }
+  for (auto& r : h->rho_l) {
+    void* dx = (unsigned char*)arena + pos;
+    memcpy(host.data() + pos, r.x_off.data(), r.x_off.size() * 8);
+    pos += r.x_off.size() * 8;
+    void* dt = (unsigned char*)arena + pos;
+    memcpy(host.data() + pos, r.t_off.data(), r.t_off.size() * 8);
+    pos += r.t_off.size() * 8;
+    r.d_x = (const int64_t*)dx;
+    r.d_t = (const int64_t*)dt;
+  }
+  TN_CUDA_TRY(cudaMemcpyAsync(arena, host.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+// ------------------------------------------------------------- profiling
+enum { P_BP = 0, P_NORM, P_ENV, P_SOLVE, P_REBUILD, P_COPY, P_PHYS, P_RHO, P_NCLS };
+const char* kProfNames[P_NCLS] = {"bp_contract", "bp_normalise", "gate_env", "trunc_solve",
+                                  "gate_rebuild", "copyback", "phys_gate", "rho"};
+
+cudaEvent_t next_event(tn_handle* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+tn_status prof_flush(tn_handle* h) {
+  if (h->prof_pending.empty()) return TN_OK;
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (auto& p : h->prof_pending) {
+    float ms = 0.f;
+    TN_CUDA_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
+    h->prof.launches[p.cls] += 1;
+    h->prof.ms[p.cls] += ms;
+    h->prof.flops[p.cls] += p.flops;
+    h->prof.bytes[p.cls] += p.bytes;
+  }
+  h->prof_pending.clear();
+  h->ev_used = 0;
+  return TN_OK;
+}
+
+// Record an event before a launch (returns the pending index or -1).
+int prof_begin(tn_handle* h, int cls) {
+  if (!h->prof_on) return -1;
+  if (h->ev_used + 2 > 8192) prof_flush(h);
+  tn_handle::ProfEv p;
+  p.cls = cls;
+  p.a = next_event(h);
+  p.b = next_event(h);
+  p.flops = p.bytes = 0;
+  if (!p.a || !p.b) return -1;
+  cudaEventRecord(p.a, h->stream);
+  h->prof_pending.push_back(p);
+  return (int)h->prof_pending.size() - 1;
+}
+
+void prof_end(tn_handle* h, int idx, double flops, double bytes) {
+  if (idx < 0) return;
+  auto& p = h->prof_pending[idx];
+  p.flops = flops;
+  p.bytes = bytes;
+  cudaEventRecord(p.b, h->stream);
+}
+
+// Algorithmic work of a GEMM launch: 8 real flops per complex MAC; bytes of
+// each operand element read once and each output written once (complex64).
+void gemm_work(const GemmDesc& d, double* flops, double* bytes) {
+  const double M = d.M, N = d.N, K = (double)d.K1 * d.K2;
+  const double bo = d.n_outer, bi = d.n_inner;
+  *flops = 8.0 * M * N * K * bo * bi;
+  const double a = M * K * bo * (d.a_in ? bi : 1.0);
+  const double b = K * N * bo * (d.b_in ? bi : 1.0);
+  const double c = M * N * bo * bi;
+  *bytes = 8.0 * (a + b + c);
+}
+
+tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
+  for (auto& L : P.L) {
+    const int pi = prof_begin(h, cls);
+    TN_CUDA_TRY(launch_cgemm(L.d, h->stream));
+    if (pi >= 0) {
+      double f, b;
+      gemm_work(L.d, &f, &b);
+      prof_end(h, pi, f, b);
+    }
+    h->stats.kernel_launches++;
+  }
+  return TN_OK;
+}
+
+const float* site_ptr(const tn_handle* h, const float* base, int v) { return base + h->t_off[v]; }
+const float* msg_ptr(const tn_handle* h, const float* base, int did) {
+  return base + (int64_t)did * 2 * h->chi * h->chi;
+}
+// incoming message into v along edge e
+const float* in_msg(const tn_handle* h, int v, int e) {
+  return msg_ptr(h, h->msg, dir_id(h->g, h->g.other(e, v), e));
+}
+
+using Ent = std::array<const float*, 3>;
+
+void build_sweep_plan(tn_handle* h) {
+  const int chi = h->chi, prec = h->cfg.prec;
+  Plan& P = h->sweep;
+  const HostGraph& g = h->g;
+  // degree 3: Yc, Ybc -> out_0; Yac -> out_1; Ya, Yab -> out_2
+  std::vector<Ent> m1, m2, c0, m3, c1, m4, m5, c2;
+  for (int v : h->sites_by_deg[3]) {
+    const auto& lg = g.legs[v];
+    const float* T = site_ptr(h, h->T, v);
+    const float* Y1 = site_ptr(h, h->Y1, v);
+    const float* Y2 = site_ptr(h, h->Y2, v);
+    m1.push_back({T, in_msg(h, v, lg[2]), Y1});
+    m2.push_back({Y1, in_msg(h, v, lg[1]), Y2});
+    c0.push_back({Y2, T, msg_ptr(h, h->raw, dir_id(g, v, lg[0]))});
+  }
+  add_mode_product(P, 3, 2, chi, prec, m1);
+  add_mode_product(P, 3, 1, chi, prec, m2);
+  add_close(P, 3, 0, chi, false, prec, c0);
+  for (int v : h->sites_by_deg[3]) {
+    const auto& lg = g.legs[v];
+    const float* T = site_ptr(h, h->T, v);
+    const float* Y1 = site_ptr(h, h->Y1, v);
+    const float* Y2 = site_ptr(h, h->Y2, v);
+    m3.push_back({Y1, in_msg(h, v, lg[0]), Y2});
+    c1.push_back({Y2, T, msg_ptr(h, h->raw, dir_id(g, v, lg[1]))});
+  }
+  add_mode_product(P, 3, 0, chi, prec, m3);
+  add_close(P, 3, 1, chi, false, prec, c1);
+  for (int v : h->sites_by_deg[3]) {
+    const auto& lg = g.legs[v];
+    const float* T = site_ptr(h, h->T, v);
+    const float* Y1 = site_ptr(h, h->Y1, v);
+    const float* Y2 = site_ptr(h, h->Y2, v);
+    m4.push_back({T, in_msg(h, v, lg[0]), Y1});
+    m5.push_back({Y1, in_msg(h, v, lg[1]), Y2});
+    c2.push_back({Y2, T, msg_ptr(h, h->raw, dir_id(g, v, lg[2]))});
+  }
+  add_mode_product(P, 3, 0, chi, prec, m4);
+  add_mode_product(P, 3, 1, chi, prec, m5);
+  add_close(P, 3, 2, chi, false, prec, c2);
+  // degree 2: Ya -> out_1 ; Yb -> out_0
+  std::vector<Ent> a1, ac1, a2, ac0;
+  for (int v : h->sites_by_deg[2]) {
+    const auto& lg = g.legs[v];
+    const float* T = site_ptr(h, h->T, v);
+    a1.push_back({T, in_msg(h, v, lg[0]), site_ptr(h, h->Y1, v)});
+    ac1.push_back({site_ptr(h, h->Y1, v), T, msg_ptr(h, h->raw, dir_id(g, v, lg[1]))});
+    a2.push_back({T, in_msg(h, v, lg[1]), site_ptr(h, h->Y2, v)});
+    ac0.push_back({site_ptr(h, h->Y2, v), T, msg_ptr(h, h->raw, dir_id(g, v, lg[0]))});
+  }
+  add_mode_product(P, 2, 0, chi, prec, a1);
+  add_close(P, 2, 1, chi, false, prec, ac1);
+  add_mode_product(P, 2, 1, chi, prec, a2);
+  add_close(P, 2, 0, chi, false, prec, ac0);
+  // degree 1
+  std::vector<Ent> d1;
+  for (int v : h->sites_by_deg[1]) {
+    const float* T = site_ptr(h, h->T, v);
+    d1.push_back({T, T, msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][0]))});
+  }
+  add_close(P, 1, 0, chi, false, prec, d1);
+}
+
+// Environments of both sides of every edge in layer `li`, open p, into gram.
+void build_gate_plans(tn_handle* h, int li) {
+  const int chi = h->chi, prec = h->cfg.prec;
+  const HostGraph& g = h->g;
+  const auto& layer = g.layers[li];
+  const int64_t c2 = (int64_t)chi * chi;
+  Plan env, reb;
+  // group sides by (degree, leg position)
+  std::vector<std::array<int, 3>> sides[4][3];  // (v, slot, side)
+  for (int s = 0; s < (int)layer.size(); ++s) {
+    const int e = layer[s];
+    const int ends[2] = {g.eu[e], g.ew[e]};
+    for (int side = 0; side < 2; ++side) {
+      const int v = ends[side];
+      sides[g.degree(v)][g.leg_pos(v, e)].push_back({v, s, side});
+    }
+  }
+  auto gram_ptr = [&](int slot, int side) { return h->gram + ((int64_t)slot * 2 + side) * 4 * c2; };
+  auto dmat_ptr = [&](int slot, int side, int p) {
+    return h->dmat + ((int64_t)slot * 2 + side) * 4 * c2 + p * 2 * c2;
+  };
+  // degree 1
+  {
+    std::vector<Ent> c;
+    for (auto& s : sides[1][0]) {
+      const float* T = site_ptr(h, h->T, s[0]);
+      c.push_back({T, T, gram_ptr(s[1], s[2])});
+    }
+    add_close(env, 1, 0, chi, true, prec, c);
+  }
+  // degree 2, gate on leg 1: Ya = T x_0 M0 ; gate on leg 0: Yb = T x_1 M1
+  {
+    std::vector<Ent> m, c;
+    for (auto& s : sides[2][1]) {
+      const int v = s[0];
+      const float* T = site_ptr(h, h->T, v);
+      m.push_back({T, in_msg(h, v, g.legs[v][0]), site_ptr(h, h->Y1, v)});
+      c.push_back({site_ptr(h, h->Y1, v), T, gram_ptr(s[1], s[2])});
+    }
+    add_mode_product(env, 2, 0, chi, prec, m);
+    add_close(env, 2, 1, chi, true, prec, c);
+    m.clear(); c.clear();
+    for (auto& s : sides[2][0]) {
+      const int v = s[0];
+      const float* T = site_ptr(h, h->T, v);
+      m.push_back({T, in_msg(h, v, g.legs[v][1]), site_ptr(h, h->Y1, v)});
+      c.push_back({site_ptr(h, h->Y1, v), T, gram_ptr(s[1], s[2])});
+    }
+    add_mode_product(env, 2, 1, chi, prec, m);
+    add_close(env, 2, 0, chi, true, prec, c);
+  }
+  // degree 3
+  for (int j = 0; j < 3; ++j) {
+    std::vector<Ent> m1, m2, c;
+    // contract the two legs other than j: first the higher one, then the lower
+    int o[2];
+    int k = 0;
+    for (int q = 2; q >= 0; --q)
+      if (q != j) o[k++] = q;
+    for (auto& s : sides[3][j]) {
+      const int v = s[0];
+      const float* T = site_ptr(h, h->T, v);
+      m1.push_back({T, in_msg(h, v, g.legs[v][o[0]]), site_ptr(h, h->Y1, v)});
+      m2.push_back({site_ptr(h, h->Y1, v), in_msg(h, v, g.legs[v][o[1]]), site_ptr(h, h->Y2, v)});
+      c.push_back({site_ptr(h, h->Y2, v), T, gram_ptr(s[1], s[2])});
+    }
+    add_mode_product(env, 3, o[0], chi, prec, m1);
+    add_mode_product(env, 3, o[1], chi, prec, m2);
+    add_close(env, 3, j, chi, true, prec, c);
+  }
+  // rebuild: T'_p = T_p x_leg D_p, into Ts; then copy back
+  std::vector<CopyLaunch> cps(4);
+  for (int d = 1; d <= 3; ++d)
+    for (int j = 0; j < d; ++j) {
+      std::vector<Ent> ent;
+      for (auto& s : sides[d][j]) {
+        const int v = s[0];
+        const int64_t len = h->t_len[v];
+        for (int p = 0; p < 2; ++p)
+          ent.push_back({site_ptr(h, h->T, v) + p * len, dmat_ptr(s[1], s[2], p),
+                         site_ptr(h, h->Ts, v) + p * len});
+        cps[d].dst.push_back(h->T + h->t_off[v]);
+        cps[d].src.push_back(h->Ts + h->t_off[v]);
+        cps[d].n_floats = 4 * len;
+      }
+      add_leg_matrix(reb, d, j, chi, prec, ent);
+    }
+  h->gate_env[li] = std::move(env);
+  h->rebuild[li] = std::move(reb);
+  std::vector<CopyLaunch> keep;
+  for (int d = 1; d <= 3; ++d)
+    if (!cps[d].dst.empty()) keep.push_back(std::move(cps[d]));
+  h->copyback[li] = std::move(keep);
+}
+
+void build_rho_plan(tn_handle* h) {
+  const int chi = h->chi, prec = h->cfg.prec;
+  const HostGraph& g = h->g;
+  Plan& P = h->rho_prep;
+  std::vector<Ent> a, b, c;
+  // degree 3: Y1 = T x_2 M2 ; Y2 = Y1 x_1 M1 ; Y1 = Y2 x_0 M0
+  for (int v : h->sites_by_deg[3]) {
+    const auto& lg = g.legs[v];
+    a.push_back({site_ptr(h, h->T, v), in_msg(h, v, lg[2]), site_ptr(h, h->Y1, v)});
+    b.push_back({site_ptr(h, h->Y1, v), in_msg(h, v, lg[1]), site_ptr(h, h->Y2, v)});
+    c.push_back({site_ptr(h, h->Y2, v), in_msg(h, v, lg[0]), site_ptr(h, h->Y1, v)});
+  }
+  add_mode_product(P, 3, 2, chi, prec, a);
+  add_mode_product(P, 3, 1, chi, prec, b);
+  add_mode_product(P, 3, 0, chi, prec, c);
+  a.clear(); b.clear();
+  // degree 2: Y1 = T x_0 M0 ; Y2 = Y1 x_1 M1 -> result in Y2, copy pointer for rho
+  for (int v : h->sites_by_deg[2]) {
+    const auto& lg = g.legs[v];
+    a.push_back({site_ptr(h, h->T, v), in_msg(h, v, lg[0]), site_ptr(h, h->Y2, v)});
+    b.push_back({site_ptr(h, h->Y2, v), in_msg(h, v, lg[1]), site_ptr(h, h->Y1, v)});
+  }
+  add_mode_product(P, 2, 0, chi, prec, a);
+  add_mode_product(P, 2, 1, chi, prec, b);
+  a.clear();
+  for (int v : h->sites_by_deg[1])
+    a.push_back({site_ptr(h, h->T, v), in_msg(h, v, g.legs[v][0]), site_ptr(h, h->Y1, v)});
+  add_mode_product(P, 1, 0, chi, prec, a);
+  // every degree ends with X in Y1
+  for (int d = 1; d <= 3; ++d) {
+    if (h->sites_by_deg[d].empty()) continue;
+    RhoLaunch r;
+    r.deg = d;
+    for (int v : h->sites_by_deg[d]) {
+      r.sites.push_back(v);
+      r.x_off.push_back(h->t_off[v]);
+      r.t_off.push_back(h->t_off[v]);
+    }
+    h->rho_l.push_back(std::move(r));
+  }
+}
+
+// --------------------------------------------------------------- execution
+tn_status check_flags(tn_handle* h, const char* where) {
+  int f = 0;
+  TN_CUDA_TRY(cudaMemcpyAsync(&f, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (f) {
+    TN_CUDA_TRY(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    set_error(std::string("non-finite or zero-norm values detected in ") + where);
+    return TN_ENUMERIC;
+  }
+  return TN_OK;
+}
+
+tn_status phys_gate(tn_handle* h, const double u[8]) {
+  for (int d = 1; d <= 3; ++d) {
+    if (!h->n_by_deg[d]) continue;
+    const int64_t len = ipow(h->chi, d);
+    const int pi = prof_begin(h, P_PHYS);
+    TN_CUDA_TRY(launch_phys_gate(h->T, h->site_offs_by_deg[d], h->n_by_deg[d], len, 2 * len,
+                                 (float)u[0], (float)u[1], (float)u[2], (float)u[3], (float)u[4],
+                                 (float)u[5], (float)u[6], (float)u[7], h->stream));
+    prof_end(h, pi, 28.0 * len * h->n_by_deg[d], 2.0 * 16.0 * len * h->n_by_deg[d]);
+    h->stats.kernel_launches++;
+  }
+  return TN_OK;
+}
+
+void rx_matrix(double theta, double u[8]) {
+  const double c = cos(theta / 2), s = sin(theta / 2);
+  // [[c, -i s], [-i s, c]]
+  u[0] = c; u[1] = 0; u[2] = 0; u[3] = -s;
+  u[4] = 0; u[5] = -s; u[6] = c; u[7] = 0;
+}
+
+double default_svd_cut(const tn_handle* h) {
+  if (h->cfg.svd_cutoff > 0) return h->cfg.svd_cutoff;
+  return h->cfg.prec == TN_FP32 || h->cfg.prec == TN_TF32X3 || h->cfg.prec == TN_BF16X3 ? 1e-6
+                                                                                       : 1e-4;
+}
+
+// Residual below which FP32-stored messages can no longer improve.
+double precision_floor(const tn_handle* h) {
+  switch (h->cfg.prec) {
+    case TN_TF32: return 2e-3;
+    case TN_BF16: return 2e-2;
+    default: return 2e-6;
+  }
+}
+
+tn_status gate_layer(tn_handle* h, int li, int sign) {
+  tn_status st = run_plan(h, h->gate_env[li], P_ENV);
+  if (st) return st;
+  SolveArgs a;
+  a.n_edges = (int)h->g.layers[li].size();
+  a.chi = h->chi;
+  a.sign = sign;
+  a.gram_cut = 1e-13;
+  a.svd_cut = default_svd_cut(h);
+  a.gram = h->gram;
+  a.dmat = h->dmat;
+  a.msg = h->msg;
+  a.msg_vw = h->d_layer_msg_vw[li];
+  a.work = h->work;
+  a.stats = h->solve_stats;
+  a.flags = h->flags;
+  a.max_sweeps = 30;
+  {
+    const int pi = prof_begin(h, P_SOLVE);
+    TN_CUDA_TRY(launch_solve(a, h->stream));
+    const double n = 2.0 * h->chi;
+    prof_end(h, pi, 40.0 * n * n * n * a.n_edges, 4.0 * 16.0 * h->chi * h->chi * a.n_edges);
+  }
+  h->stats.kernel_launches++;
+  st = run_plan(h, h->rebuild[li], P_REBUILD);
+  if (st) return st;
+  for (auto& c : h->copyback[li]) {
+    const int pi = prof_begin(h, P_COPY);
+    TN_CUDA_TRY(launch_copy_blocks(c.d_dst, c.d_src, (int)c.dst.size(), c.n_floats, h->stream));
+    prof_end(h, pi, 0.0, 8.0 * c.n_floats * c.dst.size());
+    h->stats.kernel_launches++;
+  }
+  // discarded weights of this layer
+  const int ne = a.n_edges;
+  TN_CUDA_TRY(cudaMemcpyAsync(h->h_stats, h->solve_stats, sizeof(double) * 4 * ne,
+                              cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < ne; ++i) {
+    const double dw = h->h_stats[4 * i];
+    h->stats.discarded_sum += dw;
+    h->stats.discarded_max = std::max(h->stats.discarded_max, dw);
+  }
+  return check_flags(h, "the truncation solve");
+}
+
+tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, double* res) {
+  const int nmsg = 2 * (int)h->g.eu.size();
+  // Messages are stored in FP32: once the residual is down at the rounding
+  // floor of the arithmetic it stops decreasing.  Below `floor`, a sweep that
+  // fails to halve the residual of three sweeps before ends the iteration as
+  // converged (the FP64 tolerance cannot be met by FP32 messages).
+  const double floor = precision_floor(h);
+  double r = INFINITY;
+  std::vector<double> hist;
+  bool stagnated = false;
+  int it = 0;
+  for (it = 1; it <= max_iters; ++it) {
+    TN_CUDA_TRY(cudaMemsetAsync(h->res_bits, 0, sizeof(unsigned long long), h->stream));
+    tn_status st = run_plan(h, h->sweep, P_BP);
+    if (st) return st;
+    const int pi = prof_begin(h, P_NORM);
+    TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream));
+    prof_end(h, pi, 0.0, 3.0 * 8.0 * h->chi * h->chi * nmsg);
+    h->stats.kernel_launches++;
+    unsigned long long bits = 0;
+    TN_CUDA_TRY(cudaMemcpyAsync(&bits, h->res_bits, sizeof(bits), cudaMemcpyDeviceToHost,
+                                h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    memcpy(&r, &bits, sizeof(r));
+    st = check_flags(h, "a BP sweep");
+    if (st) return st;
+    if (r < tol) break;
+    hist.push_back(r);
+    const size_t k = hist.size();
+    if (r < floor && k >= 4 && r > 0.5 * hist[k - 4]) {
+      stagnated = true;
+      break;
+    }
+  }
+  if (it > max_iters) it = max_iters;
+  h->stats.bp_iters_last = it;
+  h->stats.bp_iters_total += it;
+  h->stats.bp_residual_last = r;
+  if (iters) *iters = it;
+  if (res) *res = r;
+  if (!(r < tol) && !stagnated) {
+    set_error("BP did not reach the tolerance within max_iters");
+    return TN_ENOTCONVERGED;
+  }
+  return TN_OK;
+}
+
+tn_status compute_rho(tn_handle* h, std::vector<double>* rho_out) {
+  tn_status st = run_plan(h, h->rho_prep, P_RHO);
+  if (st) return st;
+  const int n = h->g.n;
+  int base = 0;
+  std::vector<int> order;
+  for (auto& r : h->rho_l) {
+    const int64_t len = ipow(h->chi, r.deg);
+    const int pi = prof_begin(h, P_RHO);
+    TN_CUDA_TRY(launch_rho(h->Y1, h->T, r.d_x, r.d_t, (int)r.sites.size(), len, 2 * len,
+                           h->rho + 8 * base, h->stream));
+    prof_end(h, pi, 32.0 * len * r.sites.size(), 2.0 * 16.0 * len * r.sites.size());
+    h->stats.kernel_launches++;
+    for (int v : r.sites) order.push_back(v);
+    base += (int)r.sites.size();
+  }
+  std::vector<double> tmp(8 * n);
+  TN_CUDA_TRY(cudaMemcpyAsync(tmp.data(), h->rho, sizeof(double) * 8 * n,
+                              cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  rho_out->assign(8 * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < 8; ++c) (*rho_out)[8 * order[i] + c] = tmp[8 * i + c];
+  return TN_OK;
+}
+
+double pauli_from_rho(const double* r, char p) {
+  // r: [(00) re im, (01) re im, (10) re im, (11) re im]; <P> = Tr(rho P)/Tr(rho)
+  const double tr = r[0] + r[6];
+  switch (p) {
+    case 'X': return (r[2] + r[4]) / tr;
+    case 'Y': return (-r[3] + r[5]) / tr;  // Tr(rho Y) = i rho01 - i rho10 (real part)
+    case 'Z': return (r[0] - r[6]) / tr;
+    default: return NAN;
+  }
+}
+
+tn_status init_state(tn_handle* h) {
+  TN_CUDA_TRY(cudaMemsetAsync(h->T, 0, sizeof(float) * h->t_floats, h->stream));
+  const int64_t c2 = (int64_t)h->chi * h->chi;
+  const int nmsg = 2 * (int)h->g.eu.size();
+  TN_CUDA_TRY(cudaMemsetAsync(h->msg, 0, sizeof(float) * nmsg * 2 * c2, h->stream));
+  const float one = 1.f;
+  for (int v = 0; v < h->g.n; ++v)
+    TN_CUDA_TRY(cudaMemcpyAsync(h->T + h->t_off[v], &one, sizeof(float), cudaMemcpyHostToDevice,
+                                h->stream));
+  for (int m = 0; m < nmsg; ++m)
+    TN_CUDA_TRY(cudaMemcpyAsync(h->msg + (int64_t)m * 2 * c2, &one, sizeof(float),
+                                cudaMemcpyHostToDevice, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+size_t footprint_of(const HostGraph& g, int chi) {
+  int64_t tf = 0;
+  for (int v = 0; v < g.n; ++v) tf += 4 * ipow(chi, g.degree(v));
+  const int64_t c2 = (int64_t)chi * chi;
+  size_t maxl = 0;
+  for (auto& l : g.layers) maxl = std::max(maxl, l.size());
+  size_t b = 0;
+  b += 4 * sizeof(float) * (size_t)tf;                      // T, Ts, Y1, Y2
+  b += 2 * sizeof(float) * (size_t)(2 * g.eu.size()) * 2 * c2;  // msg, raw
+  b += 2 * sizeof(float) * maxl * 8 * c2;                  // gram, dmat
+  b += sizeof(double) * maxl * solve_work_doubles(chi);    // work
+  return b;
+}
+
+}  // namespace
+}  // namespace tnbp
+
+using namespace tnbp;
+
+extern "C" {
+
+const char* tn_last_error(void) { return g_err.c_str(); }
+const char* tn_version(void) { return "tnbp 0.1 (sm_103a)"; }
+
+tn_status tn_heavy_hex(int32_t rows, int32_t cols, int32_t* n_vertices, int32_t* n_edges,
+                       int32_t* edges_out, uint8_t* colours_out, int32_t capacity) {
+  HostGraph g;
+  std::string why;
+  if (!heavy_hex(rows, cols, &g, &why)) {
+    set_error(why);
+    return TN_EINVAL;
+  }
+  const int m = (int)g.eu.size();
+  if (n_vertices) *n_vertices = g.n;
+  if (n_edges) *n_edges = m;
+  if (edges_out || colours_out) {
+    if (capacity < m) {
+      set_error("capacity smaller than the number of edges");
+      return TN_EINVAL;
+    }
+    for (int e = 0; e < m; ++e) {
+      if (edges_out) { edges_out[2 * e] = g.eu[e]; edges_out[2 * e + 1] = g.ew[e]; }
+      if (colours_out) colours_out[e] = (uint8_t)g.colour[e];
+    }
+  }
+  return TN_OK;
+}
+
+tn_status tn_footprint_estimate(const tn_graph* graph, const tn_config* cfg, size_t* out) {
+  if (!graph || !cfg || !out) { set_error("null argument"); return TN_EINVAL; }
+  HostGraph g;
+  std::string why;
+  if (!build_graph(graph->n_vertices, graph->n_edges, graph->edges, graph->colour, &g, &why)) {
+    set_error(why);
+    return TN_EINVAL;
+  }
+  *out = footprint_of(g, cfg->chi);
+  return TN_OK;
+}
+
+tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_allocator* alloc,
+                    void* cuda_stream, tn_handle** out) {
+  if (!graph || !cfg || !out) { set_error("null argument"); return TN_EINVAL; }
+  *out = nullptr;
+  if (cfg->chi < 1 || cfg->chi > 256) { set_error("chi must be in 1..256"); return TN_EINVAL; }
+  if (cfg->prec < TN_FP32 || cfg->prec > TN_TF32X3) { set_error("unknown precision"); return TN_EINVAL; }
+  if (cfg->prec != TN_FP32) { set_error("precision mode not built yet"); return TN_EUNSUPPORTED; }
+  if (!(cfg->bp_tol > 0) || cfg->bp_max_iters < 1) {
+    set_error("bp_tol must be > 0 and bp_max_iters >= 1");
+    return TN_EINVAL;
+  }
+  if (alloc && (!alloc->alloc || !alloc->free)) { set_error("allocator callbacks missing"); return TN_EINVAL; }
+  tn_handle* h = new tn_handle();
+  std::string why;
+  if (!build_graph(graph->n_vertices, graph->n_edges, graph->edges, graph->colour, &h->g, &why)) {
+    set_error(why);
+    delete h;
+    return TN_EINVAL;
+  }
+  {
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaGetDeviceProperties(&prop, dev);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
+      delete h;
+      return TN_ECUDA;
+    }
+    if (prop.major * 10 + prop.minor != 103) {
+      set_error("device is sm_" + std::to_string(prop.major * 10 + prop.minor) +
+                "; this library is built for sm_103a");
+      delete h;
+      return TN_ECUDA;
+    }
+  }
+  h->cfg = *cfg;
+  h->chi = cfg->chi;
+  h->stream = (cudaStream_t)cuda_stream;
+  if (alloc) { h->alloc = *alloc; h->own_alloc = false; }
+  const HostGraph& g = h->g;
+  const int chi = h->chi;
+  const int64_t c2 = (int64_t)chi * chi;
+  h->t_off.resize(g.n);
+  h->t_len.resize(g.n);
+  int64_t off = 0;
+  for (int v = 0; v < g.n; ++v) {
+    h->t_off[v] = off;
+    h->t_len[v] = ipow(chi, g.degree(v));
+    off += 4 * h->t_len[v];
+    h->sites_by_deg[g.degree(v)].push_back(v);
+  }
+  h->t_floats = off;
+  const int nmsg = 2 * (int)g.eu.size();
+  for (auto& l : g.layers) h->max_layer = std::max(h->max_layer, (int)l.size());
+  auto fail = [&](tn_status s) { dev_free_all(h); delete h; return s; };
+  h->T = (float*)dev_alloc(h, sizeof(float) * off);
+  h->Ts = (float*)dev_alloc(h, sizeof(float) * off);
+  h->Y1 = (float*)dev_alloc(h, sizeof(float) * off);
+  h->Y2 = (float*)dev_alloc(h, sizeof(float) * off);
+  h->msg = (float*)dev_alloc(h, sizeof(float) * nmsg * 2 * c2);
+  h->raw = (float*)dev_alloc(h, sizeof(float) * nmsg * 2 * c2);
+  h->gram = (float*)dev_alloc(h, sizeof(float) * h->max_layer * 8 * c2);
+  h->dmat = (float*)dev_alloc(h, sizeof(float) * h->max_layer * 8 * c2);
+  h->work = (double*)dev_alloc(h, sizeof(double) * h->max_layer * solve_work_doubles(chi));
+  h->solve_stats = (double*)dev_alloc(h, sizeof(double) * 4 * h->max_layer);
+  h->res_bits = (unsigned long long*)dev_alloc(h, 64);
+  h->flags = (int*)dev_alloc(h, 64);
+  h->rho = (double*)dev_alloc(h, sizeof(double) * 8 * g.n);
+  for (int d = 1; d <= 3; ++d) {
+    h->n_by_deg[d] = (int)h->sites_by_deg[d].size();
+    h->site_offs_by_deg[d] = (int64_t*)dev_alloc(h, sizeof(int64_t) * (h->n_by_deg[d] + 1));
+  }
+  const int nl = (int)g.layers.size();
+  h->d_layer_msg_vw.resize(nl);
+  h->layer_msg_vw.resize(nl);
+  for (int li = 0; li < nl; ++li) {
+    h->d_layer_msg_vw[li] = (int32_t*)dev_alloc(h, sizeof(int32_t) * 2 * g.layers[li].size());
+    if (!h->d_layer_msg_vw[li]) {
+      set_error("device allocation of layer tables failed");
+      return fail(TN_ENOMEM);
+    }
+  }
+  if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->msg || !h->raw || !h->gram || !h->dmat ||
+      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho) {
+    set_error("device allocation failed (footprint " + std::to_string(footprint_of(g, chi)) +
+              " bytes)");
+    return fail(TN_ENOMEM);
+  }
+  for (int d = 1; d <= 3; ++d) {
+    std::vector<int64_t> offs;
+    for (int v : h->sites_by_deg[d]) offs.push_back(h->t_off[v]);
+    if (!offs.empty() &&
+        cudaMemcpy(h->site_offs_by_deg[d], offs.data(), sizeof(int64_t) * offs.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("upload of site offsets failed");
+      return fail(TN_ECUDA);
+    }
+  }
+  for (int li = 0; li < nl; ++li) {
+    auto& v = h->layer_msg_vw[li];
+    for (int e : g.layers[li]) {
+      v.push_back(dir_id(g, g.eu[e], e));
+      v.push_back(dir_id(g, g.ew[e], e));
+    }
+    if (cudaMemcpy(h->d_layer_msg_vw[li], v.data(), sizeof(int32_t) * v.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("upload of layer tables failed");
+      return fail(TN_ECUDA);
+    }
+  }
+  cudaMemset(h->flags, 0, 64);
+  h->h_stats = new double[4 * std::max(1, h->max_layer)];
+  build_sweep_plan(h);
+  h->gate_env.resize(nl);
+  h->rebuild.resize(nl);
+  h->copyback.resize(nl);
+  for (int li = 0; li < nl; ++li) build_gate_plans(h, li);
+  build_rho_plan(h);
+  tn_status st = upload_plans(h);
+  if (st) { delete[] h->h_stats; return fail(st); }
+  st = init_state(h);
+  if (st) { delete[] h->h_stats; return fail(st); }
+  *out = h;
+  return TN_OK;
+}
+
+tn_status tn_destroy(tn_handle* h) {
+  if (!h) return TN_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  dev_free_all(h);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  delete[] h->h_stats;
+  delete h;
+  return TN_OK;
+}
+
+tn_status tn_profile_enable(tn_handle* h, int32_t on) {
+  if (!h) { set_error("null handle"); return TN_EINVAL; }
+  tn_status st = prof_flush(h);
+  if (st) return st;
+  h->prof = tn_profile{};
+  h->prof.n_classes = P_NCLS;
+  h->prof_on = on != 0;
+  return TN_OK;
+}
+
+tn_status tn_profile_read(tn_handle* h, tn_profile* out) {
+  if (!h || !out) { set_error("null argument"); return TN_EINVAL; }
+  tn_status st = prof_flush(h);
+  if (st) return st;
+  h->prof.n_classes = P_NCLS;
+  *out = h->prof;
+  return TN_OK;
+}
+
+const char* tn_profile_class_name(int32_t cls) {
+  if (cls < 0 || cls >= P_NCLS) return "";
+  return kProfNames[cls];
+}
+
+static tn_status evolve(tn_handle* h, double theta, int steps, bool clifford_dagger) {
+  if (!h) { set_error("null handle"); return TN_EINVAL; }
+  if (steps < 0) { set_error("steps must be >= 0"); return TN_EINVAL; }
+  h->stats = tn_stats{};
+  tn_status worst = TN_OK;
+  double u[8];
+  rx_matrix(clifford_dagger ? -M_PI / 2 : theta, u);
+  for (int s = 0; s < steps; ++s) {
+    tn_status st;
+    if (!clifford_dagger) {
+      st = phys_gate(h, u);
+      if (st) return st;
+    }
+    for (int li = 0; li < (int)h->g.layers.size(); ++li) {
+      st = gate_layer(h, li, clifford_dagger ? -1 : +1);
+      if (st) return st;
+    }
+    if (clifford_dagger) {
+      st = phys_gate(h, u);
+      if (st) return st;
+    }
+    st = bp_converge_impl(h, h->cfg.bp_tol, h->cfg.bp_max_iters, nullptr, nullptr);
+    if (st == TN_ENOTCONVERGED) worst = st;
+    else if (st) return st;
+    h->stats.steps_done = s + 1;
+  }
+  if (worst) set_error("a BP regauge hit bp_max_iters");
+  return worst;
+}
+
+tn_status tn_apply_floquet(tn_handle* h, double theta_h, int32_t steps) {
+  return evolve(h, theta_h, steps, false);
+}
+
+tn_status tn_apply_clifford_dagger(tn_handle* h, int32_t steps) {
+  return evolve(h, 0.0, steps, true);
+}
+
+tn_status tn_bp_converge(tn_handle* h, double tol, int32_t max_iters, int32_t* iters_out,
+                         double* residual_out) {
+  if (!h) { set_error("null handle"); return TN_EINVAL; }
+  if (!(tol > 0) || max_iters < 1) { set_error("tol must be > 0, max_iters >= 1"); return TN_EINVAL; }
+  h->stats = tn_stats{};
+  int it = 0;
+  double r = 0;
+  tn_status st = bp_converge_impl(h, tol, max_iters, &it, &r);
+  if (iters_out) *iters_out = it;
+  if (residual_out) *residual_out = r;
+  return st;
+}
+
+tn_status tn_expect_z_all(tn_handle* h, double* out) {
+  if (!h || !out) { set_error("null argument"); return TN_EINVAL; }
+  std::vector<double> rho;
+  tn_status st = compute_rho(h, &rho);
+  if (st) return st;
+  for (int v = 0; v < h->g.n; ++v) out[v] = pauli_from_rho(&rho[8 * v], 'Z');
+  return TN_OK;
+}
+
+static tn_status backup_state(tn_handle* h, bool restore) {
+  const int64_t c2 = (int64_t)h->chi * h->chi;
+  const size_t mb = sizeof(float) * 2 * h->g.eu.size() * 2 * c2;
+  if (!h->T_bak) {
+    h->T_bak = (float*)dev_alloc(h, sizeof(float) * h->t_floats);
+    h->msg_bak = (float*)dev_alloc(h, mb);
+    if (!h->T_bak || !h->msg_bak) { set_error("no memory for the state copy"); return TN_ENOMEM; }
+  }
+  float* dst_t = restore ? h->T : h->T_bak;
+  float* src_t = restore ? h->T_bak : h->T;
+  float* dst_m = restore ? h->msg : h->msg_bak;
+  float* src_m = restore ? h->msg_bak : h->msg;
+  TN_CUDA_TRY(cudaMemcpyAsync(dst_t, src_t, sizeof(float) * h->t_floats, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  TN_CUDA_TRY(cudaMemcpyAsync(dst_m, src_m, mb, cudaMemcpyDeviceToDevice, h->stream));
+  return TN_OK;
+}
+
+tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t method,
+                    double* out) {
+  if (!h || (!ops && n_ops > 0) || (!out && n_ops > 0)) { set_error("null argument"); return TN_EINVAL; }
+  if (method != 0 && method != 1) { set_error("method must be 0 or 1"); return TN_EINVAL; }
+  const int n = h->g.n;
+  for (int i = 0; i < n_ops; ++i) {
+    if (ops[i].weight < 1 || !ops[i].sites || !ops[i].paulis) {
+      set_error("Pauli string " + std::to_string(i) + " is empty");
+      return TN_EINVAL;
+    }
+    std::vector<int> seen(n, 0);
+    for (int j = 0; j < ops[i].weight; ++j) {
+      const int q = ops[i].sites[j];
+      const char p = ops[i].paulis[j];
+      if (q < 0 || q >= n || seen[q] || (p != 'X' && p != 'Y' && p != 'Z')) {
+        set_error("Pauli string " + std::to_string(i) + " has a bad site or letter");
+        return TN_EINVAL;
+      }
+      seen[q] = 1;
+    }
+  }
+  std::vector<double> rho;
+  bool have_rho = false;
+  for (int i = 0; i < n_ops; ++i) {
+    const tn_pauli& P = ops[i];
+    const double sgn = P.sign < 0 ? -1.0 : 1.0;
+    if (P.weight == 1) {
+      if (!have_rho) {
+        tn_status st = compute_rho(h, &rho);
+        if (st) return st;
+        have_rho = true;
+      }
+      out[i] = sgn * pauli_from_rho(&rho[8 * P.sites[0]], P.paulis[0]);
+      continue;
+    }
+    if (method == 0) {
+      set_error("region contraction of strings of weight > 1 is not built yet");
+      return TN_EUNSUPPORTED;
+    }
+    PauliString s;
+    s.ops.assign(n, 0);
+    for (int j = 0; j < P.weight; ++j)
+      s.ops[P.sites[j]] = P.paulis[j] == 'X' ? 1 : P.paulis[j] == 'Y' ? 2 : 3;
+    int site = -1, np = 0, zs = 1;
+    if (!reduce_to_single_z(s, h->g, 32, &site, &np, &zs)) {
+      set_error("string " + std::to_string(i) + " is not U^n'(pi/2) Z_i U^-n'(pi/2) for n' <= 32");
+      return TN_EUNSUPPORTED;
+    }
+    tn_status st = backup_state(h, false);
+    if (st) return st;
+    tn_stats keep = h->stats;
+    st = evolve(h, 0.0, np, true);
+    if (st && st != TN_ENOTCONVERGED) { backup_state(h, true); return st; }
+    std::vector<double> r2;
+    st = compute_rho(h, &r2);
+    tn_status st2 = backup_state(h, true);
+    h->stats = keep;
+    if (st) return st;
+    if (st2) return st2;
+    out[i] = sgn * zs * pauli_from_rho(&r2[8 * site], 'Z');
+  }
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status tn_get_stats(const tn_handle* h, tn_stats* out) {
+  if (!h || !out) { set_error("null argument"); return TN_EINVAL; }
+  *out = h->stats;
+  return TN_OK;
+}
+
+static tn_status site_io(tn_handle* h, int v, float* buf, size_t n_floats, bool get) {
+  if (!h || !buf) { set_error("null argument"); return TN_EINVAL; }
+  if (v < 0 || v >= h->g.n) { set_error("vertex out of range"); return TN_EINVAL; }
+  const int64_t len = h->t_len[v];
+  if (n_floats != (size_t)(4 * len)) { set_error("site buffer must hold 4*chi^d floats"); return TN_EINVAL; }
+  std::vector<float> planar(4 * len);
+  if (get) {
+    TN_CUDA_TRY(cudaMemcpyAsync(planar.data(), h->T + h->t_off[v], sizeof(float) * 4 * len,
+                                cudaMemcpyDeviceToHost, h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < 2 * len; ++i) {
+      buf[2 * i] = planar[i];
+      buf[2 * i + 1] = planar[2 * len + i];
+    }
+  } else {
+    for (int64_t i = 0; i < 2 * len; ++i) {
+      planar[i] = buf[2 * i];
+      planar[2 * len + i] = buf[2 * i + 1];
+    }
+    TN_CUDA_TRY(cudaMemcpyAsync(h->T + h->t_off[v], planar.data(), sizeof(float) * 4 * len,
+                                cudaMemcpyHostToDevice, h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return TN_OK;
+}
+
+tn_status tn_get_site(tn_handle* h, int32_t v, float* host_out, size_t n_floats) {
+  return site_io(h, v, host_out, n_floats, true);
+}
+tn_status tn_set_site(tn_handle* h, int32_t v, const float* host_in, size_t n_floats) {
+  return site_io(h, v, const_cast<float*>(host_in), n_floats, false);
+}
+
+static tn_status msg_io(tn_handle* h, int e, int src, float* buf, size_t n_floats, bool get) {
+  if (!h || !buf) { set_error("null argument"); return TN_EINVAL; }
+  if (e < 0 || e >= (int)h->g.eu.size() || (src != h->g.eu[e] && src != h->g.ew[e])) {
+    set_error("edge or source vertex out of range");
+    return TN_EINVAL;
+  }
+  const int64_t c2 = (int64_t)h->chi * h->chi;
+  if (n_floats != (size_t)(2 * c2)) { set_error("message buffer must hold 2*chi^2 floats"); return TN_EINVAL; }
+  float* dev = h->msg + (int64_t)dir_id(h->g, src, e) * 2 * c2;
+  std::vector<float> planar(2 * c2);
+  if (get) {
+    TN_CUDA_TRY(cudaMemcpyAsync(planar.data(), dev, sizeof(float) * 2 * c2, cudaMemcpyDeviceToHost,
+                                h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int64_t i = 0; i < c2; ++i) { buf[2 * i] = planar[i]; buf[2 * i + 1] = planar[c2 + i]; }
+  } else {
+    for (int64_t i = 0; i < c2; ++i) { planar[i] = buf[2 * i]; planar[c2 + i] = buf[2 * i + 1]; }
+    TN_CUDA_TRY(cudaMemcpyAsync(dev, planar.data(), sizeof(float) * 2 * c2, cudaMemcpyHostToDevice,
+                                h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return TN_OK;
+}
+
+tn_status tn_get_message(tn_handle* h, int32_t e, int32_t src, float* host_out, size_t n_floats) {
+  return msg_io(h, e, src, host_out, n_floats, true);
+}
+tn_status tn_set_message(tn_handle* h, int32_t e, int32_t src, const float* host_in,
+                         size_t n_floats) {
+  return msg_io(h, e, src, const_cast<float*>(host_in), n_floats, false);
+}
+
+tn_status tn_clifford_reduce(const tn_graph* graph, const tn_pauli* op, int32_t max_steps,
+                             int32_t* site_out, int32_t* nprime_out, int32_t* sign_out) {
+  if (!graph || !op || !site_out || !nprime_out || !sign_out) { set_error("null argument"); return TN_EINVAL; }
+  HostGraph g;
+  std::string why;
+  if (!build_graph(graph->n_vertices, graph->n_edges, graph->edges, graph->colour, &g, &why)) {
+    set_error(why);
+    return TN_EINVAL;
+  }
+  PauliString s;
+  s.ops.assign(g.n, 0);
+  if (op->weight < 1 || !op->sites || !op->paulis) { set_error("empty Pauli string"); return TN_EINVAL; }
+  for (int j = 0; j < op->weight; ++j) {
+    const int q = op->sites[j];
+    const char p = op->paulis[j];
+    if (q < 0 || q >= g.n || s.ops[q] || (p != 'X' && p != 'Y' && p != 'Z')) {
+      set_error("bad site or letter in the Pauli string");
+      return TN_EINVAL;
+    }
+    s.ops[q] = p == 'X' ? 1 : p == 'Y' ? 2 : 3;
+  }
+  int site = -1, np = 0, zs = 1;
+  if (!reduce_to_single_z(s, g, max_steps, &site, &np, &zs)) {
+    set_error("no n' <= max_steps reduces the string to a single Z");
+    return TN_EUNSUPPORTED;
+  }
+  *site_out = site;
+  *nprime_out = np;
+  *sign_out = zs * (op->sign < 0 ? -1 : 1);
+  return TN_OK;
+}
+
+tn_status tn_footprint(const tn_handle* h, size_t* bytes_out) {
+  if (!h || !bytes_out) { set_error("null argument"); return TN_EINVAL; }
+  *bytes_out = h->bytes;
+  return TN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,295 @@
+// CUDA-core kernels of the tnbp library: the plain-FP32 batched complex GEMM
+// that carries every contraction of the message and gate updates in the
+// TN_FP32 mode, the physical-leg gate, message normalisation with the FP64
+// residual, the single-site reduced density matrix and a batched block copy.
+#include "common.cuh"
+#include "tnbp.h"
+
+namespace tnbp {
+
+// ---------------------------------------------------------------------------
+// Plain FP32 complex GEMM, 64 x 64 output tile per CTA, 16-deep K slices
+// staged in shared memory, 4 x 4 complex outputs per thread (planar re/im
+// accumulators).  Operand loads pick the thread-to-element map that makes
+// consecutive threads read consecutive addresses of whichever index of the
+// operand is contiguous.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__device__ __forceinline__ int64_t koff(int k, int K2, int64_t s1, int64_t s2) {
+  int k1 = k / K2;
+  int k2 = k - k1 * K2;
+  return (int64_t)k1 * s1 + (int64_t)k2 * s2;
+}
+
+__global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
+  __shared__ float As[2][BK][BM + 1];
+  __shared__ float Bs[2][BK][BN + 1];
+  const int z = blockIdx.z;
+  const int outer = z / d.n_inner;
+  const int inner = z - outer * d.n_inner;
+  const float* A = d.A[outer] + inner * d.a_in;
+  const float* B = d.B[outer] + inner * d.b_in;
+  float* C = d.C[outer] + inner * d.c_in;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int K = d.K1 * d.K2;
+  const bool a_kfast = (d.a_k2 == 1);
+  const bool b_nfast = (d.b_n == 1);
+  const float sa = d.conj_a ? -1.f : 1.f;
+  const float sb = d.conj_b ? -1.f : 1.f;
+
+  float accr[4][4], acci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.f;
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int idx = tid + r * 256;
+      int mm, kk;
+      if (a_kfast) { kk = idx & (BK - 1); mm = idx >> 4; }
+      else { mm = idx & (BM - 1); kk = idx >> 6; }
+      const int m = m0 + mm, k = k0 + kk;
+      float re = 0.f, im = 0.f;
+      if (m < d.M && k < K) {
+        const int64_t off = (int64_t)m * d.a_m + koff(k, d.K2, d.a_k1, d.a_k2);
+        re = A[off];
+        im = sa * A[off + d.plane_a];
+      }
+      As[0][kk][mm] = re;
+      As[1][kk][mm] = im;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int idx = tid + r * 256;
+      int nn, kk;
+      if (b_nfast) { nn = idx & (BN - 1); kk = idx >> 6; }
+      else { kk = idx & (BK - 1); nn = idx >> 4; }
+      const int n = n0 + nn, k = k0 + kk;
+      float re = 0.f, im = 0.f;
+      if (n < d.N && k < K) {
+        const int64_t off = (int64_t)n * d.b_n + koff(k, d.K2, d.b_k1, d.b_k2);
+        re = B[off];
+        im = sb * B[off + d.plane_b];
+      }
+      Bs[0][kk][nn] = re;
+      Bs[1][kk][nn] = im;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float ar[4], ai[4], br[4], bi[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ar[i] = As[0][kk][ty + 16 * i];
+        ai[i] = As[1][kk][ty + 16 * i];
+        br[i] = Bs[0][kk][tx + 16 * i];
+        bi[i] = Bs[1][kk][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
+          accr[i][j] = fmaf(-ai[i], bi[j], accr[i][j]);
+          acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
+          acci[i][j] = fmaf(ai[i], br[j], acci[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= d.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= d.N) continue;
+      const int64_t off = (int64_t)m * d.c_m + (int64_t)n * d.c_n;
+      if (d.accumulate) {
+        C[off] += accr[i][j];
+        C[off + d.plane_c] += acci[i][j];
+      } else {
+        C[off] = accr[i][j];
+        C[off + d.plane_c] = acci[i][j];
+      }
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s) {
+  if (d.M <= 0 || d.N <= 0 || d.n_outer <= 0 || d.n_inner <= 0) return cudaSuccess;
+  dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, d.n_outer * d.n_inner);
+  cgemm_simt_kernel<<<grid, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// 2x2 gate on the physical leg of a list of sites (all of one degree).
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void phys_gate_kernel(float* T, const int64_t* site_off, int64_t len, int64_t plane,
+                                 float u00r, float u00i, float u01r, float u01i, float u10r,
+                                 float u10i, float u11r, float u11i) {
+  const int64_t base = site_off[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float* t0r = T + base + i;
+    float* t1r = T + base + len + i;
+    const float ar = t0r[0], ai = t0r[plane];
+    const float br = t1r[0], bi = t1r[plane];
+    t0r[0] = u00r * ar - u00i * ai + u01r * br - u01i * bi;
+    t0r[plane] = u00r * ai + u00i * ar + u01r * bi + u01i * br;
+    t1r[0] = u10r * ar - u10i * ai + u11r * br - u11i * bi;
+    t1r[plane] = u10r * ai + u10i * ar + u11r * bi + u11i * br;
+  }
+}
+}  // namespace
+
+cudaError_t launch_phys_gate(float* T, const int64_t* site_off, int n_sites, int64_t len,
+                             int64_t plane, float u00r, float u00i, float u01r, float u01i,
+                             float u10r, float u10i, float u11r, float u11i, cudaStream_t s) {
+  if (n_sites <= 0) return cudaSuccess;
+  int64_t bx = (len + 255) / 256;
+  if (bx > 1024) bx = 1024;
+  dim3 grid((unsigned)bx, n_sites);
+  phys_gate_kernel<<<grid, 256, 0, s>>>(T, site_off, len, plane, u00r, u00i, u01r, u01i, u10r,
+                                        u10i, u11r, u11i);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Message normalisation: Hermitise, FP64 Frobenius norm, residual vs. the
+// current message, overwrite.  One CTA per directed message.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[0] = t;
+  }
+  __syncthreads();
+  return sh[0];
+}
+
+__global__ void normalise_kernel(const float* raw, float* msg, int chi,
+                                 unsigned long long* res_bits, int* flags) {
+  __shared__ double sh[32];
+  const int64_t n2 = (int64_t)chi * chi;
+  const float* r = raw + blockIdx.x * 2 * n2;
+  float* m = msg + blockIdx.x * 2 * n2;
+  double ss = 0.0;
+  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
+    const double hr = 0.5 * ((double)r[idx] + (double)r[(int64_t)j * chi + i]);
+    const double hi = 0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]);
+    ss += hr * hr + hi * hi;
+  }
+  ss = block_sum(ss, sh);
+  const double nrm = sqrt(ss);
+  if (!(nrm > 0.0) || !isfinite(nrm)) {
+    if (threadIdx.x == 0) atomicOr(flags, 1);
+    return;
+  }
+  const double inv = 1.0 / nrm;
+  double dd = 0.0;
+  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
+    const double hr = 0.5 * ((double)r[idx] + (double)r[(int64_t)j * chi + i]) * inv;
+    const double hi = 0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]) * inv;
+    const double er = hr - (double)m[idx], ei = hi - (double)m[n2 + idx];
+    dd += er * er + ei * ei;
+  }
+  dd = block_sum(dd, sh);
+  // every thread has read m for the residual before anyone overwrites it
+  __syncthreads();
+  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
+    m[idx] = (float)(0.5 * ((double)r[idx] + (double)r[(int64_t)j * chi + i]) * inv);
+    m[n2 + idx] = (float)(0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]) * inv);
+  }
+  if (threadIdx.x == 0) {
+    const double res = sqrt(dd);
+    atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
+  }
+}
+}  // namespace
+
+cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
+                             unsigned long long* res_bits, int* flags, cudaStream_t s) {
+  if (n_msgs <= 0) return cudaSuccess;
+  normalise_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// rho[p][p'] = sum_r X[p][r] conj(T[p'][r]), FP64 accumulation, one CTA per site.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void rho_kernel(const float* X, const float* T, const int64_t* x_off,
+                           const int64_t* t_off, int64_t len, int64_t plane, double* rho) {
+  __shared__ double sh[32];
+  const float* x = X + x_off[blockIdx.x];
+  const float* t = T + t_off[blockIdx.x];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+    const double x0r = x[i], x0i = x[plane + i], x1r = x[len + i], x1i = x[plane + len + i];
+    const double t0r = t[i], t0i = t[plane + i], t1r = t[len + i], t1i = t[plane + len + i];
+    // x_p * conj(t_q)
+    acc[0] += x0r * t0r + x0i * t0i;  acc[1] += x0i * t0r - x0r * t0i;   // (0,0)
+    acc[2] += x0r * t1r + x0i * t1i;  acc[3] += x0i * t1r - x0r * t1i;   // (0,1)
+    acc[4] += x1r * t0r + x1i * t0i;  acc[5] += x1i * t0r - x1r * t0i;   // (1,0)
+    acc[6] += x1r * t1r + x1i * t1i;  acc[7] += x1i * t1r - x1r * t1i;   // (1,1)
+  }
+  for (int c = 0; c < 8; ++c) {
+    const double s = block_sum(acc[c], sh);
+    if (threadIdx.x == 0) rho[blockIdx.x * 8 + c] = s;
+  }
+}
+}  // namespace
+
+cudaError_t launch_rho(const float* X, const float* T, const int64_t* x_off,
+                       const int64_t* t_off, int n_sites, int64_t len, int64_t plane,
+                       double* rho, cudaStream_t s) {
+  if (n_sites <= 0) return cudaSuccess;
+  rho_kernel<<<n_sites, 256, 0, s>>>(X, T, x_off, t_off, len, plane, rho);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void copy_blocks_kernel(float* const* dst, const float* const* src, int64_t n4) {
+  float4* d = reinterpret_cast<float4*>(dst[blockIdx.y]);
+  const float4* s = reinterpret_cast<const float4*>(src[blockIdx.y]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+}  // namespace
+
+cudaError_t launch_copy_blocks(float* const* dst, const float* const* src, int n_blocks,
+                               int64_t n_floats, cudaStream_t s) {
+  if (n_blocks <= 0) return cudaSuccess;
+  const int64_t n4 = n_floats / 4;
+  int64_t bx = (n4 + 255) / 256;
+  if (bx > 512) bx = 512;
+  dim3 grid((unsigned)bx, n_blocks);
+  copy_blocks_kernel<<<grid, 256, 0, s>>>(dst, src, n4);
+  return cudaGetLastError();
+}
+
+}  // namespace tnbp
