@@ -202,6 +202,26 @@ tn_status tn_clifford_reduce(const tn_graph* graph, const tn_pauli* op, int32_t 
 /* tn_expect_z_all — <Z_v> for every vertex v (out: n_vertices doubles). */
 tn_status tn_expect_z_all(tn_handle* h, double* out);
 
+/*
+ * tn_truncation_solve — the FP64 truncation solve of the simple update (Methods,
+ * "The simple update procedure") as a standalone batched call on caller-owned
+ * device buffers, on `cuda_stream` (NULL: legacy default stream); returns after
+ * the stream has finished it.  For each of n_edges gate edges (v, w):
+ *   gram  [edge][side v|w][p][re|im][chi][chi] FP32 (input): the open-p
+ *         environments N_p[e, e'] = sum T[p, .., e, ..] conj(T[p, .., e', ..]) prod M
+ *         of both sides (the BP message contraction with p left open);
+ *   dmat  same shape (output): per side and p the chi x chi matrix D_p with
+ *         T'[p, .., n, ..] = sum_e T[p, .., e, ..] D_p[e][n] giving the truncated
+ *         two-site update of exp(sign i pi/4 Z Z);
+ *   s_out [edge][chi] FP64 (output): the kept singular values with ||S||_2 = 1
+ *         (zeros past the rank or below svd_cutoff * sigma_1).
+ * The FP64 workspace (12 (2 chi)^2 doubles per edge) is allocated with
+ * cudaMallocAsync on the stream and freed before return.
+ * Errors: TN_EINVAL, TN_ENUMERIC (zero or non-finite spectrum), TN_ECUDA.
+ */
+tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int32_t n_edges,
+                              int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream);
+
 /* tn_get_stats — counters of the last evolution call. */
 tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
 

@@ -87,8 +87,9 @@ struct SolveArgs {
   double svd_cut;           // relative singular-value cutoff
   const float* gram;        // [edge][side][p][plane][chi][chi]
   float* dmat;              // [edge][side][p][plane][chi][chi]
-  float* msg;               // message buffer [2E][plane][chi][chi]
+  float* msg;               // message buffer [2E][plane][chi][chi] (may be null)
   const int32_t* msg_vw;    // per edge: directed index of v->w and w->v
+  double* s_out;            // per edge: chi normalised singular values (may be null)
   double* work;             // [edge][6][n][n] complex doubles
   double* stats;            // per edge: [discarded weight, kept, sigma_1, min_gap]
   int* flags;

@@ -674,6 +674,7 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   a.stats = h->solve_stats;
   a.flags = h->flags;
   a.max_sweeps = 30;
+  a.s_out = nullptr;
   {
     const int pi = prof_begin(h, P_SOLVE);
     TN_CUDA_TRY(launch_solve(a, h->stream));
@@ -1165,6 +1166,49 @@ tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t me
     out[i] = sgn * zs * pauli_from_rho(&r2[8 * site], 'Z');
   }
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int32_t n_edges,
+                              int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream) {
+  if (!gram || !dmat || !s_out) { set_error("null argument"); return TN_EINVAL; }
+  if (n_edges < 1 || chi < 1 || 2 * chi > 512 || (sign != 1 && sign != -1)) {
+    set_error("n_edges >= 1, 1 <= chi <= 256 and sign = +-1 required");
+    return TN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t wbytes = sizeof(double) * (size_t)n_edges * solve_work_doubles(chi);
+  const size_t sbytes = sizeof(double) * 4 * (size_t)n_edges;
+  void *work = nullptr, *stats = nullptr, *flags = nullptr;
+  TN_CUDA_TRY(cudaMallocAsync(&work, wbytes, st));
+  TN_CUDA_TRY(cudaMallocAsync(&stats, sbytes, st));
+  TN_CUDA_TRY(cudaMallocAsync(&flags, sizeof(int), st));
+  TN_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(int), st));
+  SolveArgs a;
+  a.n_edges = n_edges;
+  a.chi = chi;
+  a.sign = sign;
+  a.gram_cut = 1e-13;
+  a.svd_cut = svd_cutoff > 0 ? svd_cutoff : 1e-6;
+  a.gram = gram;
+  a.dmat = dmat;
+  a.msg = nullptr;
+  a.msg_vw = nullptr;
+  a.s_out = s_out;
+  a.work = (double*)work;
+  a.stats = (double*)stats;
+  a.flags = (int*)flags;
+  a.max_sweeps = 30;
+  cudaError_t le = launch_solve(a, st);
+  int f = 0;
+  cudaError_t ce = cudaMemcpyAsync(&f, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(work, st);
+  cudaFreeAsync(stats, st);
+  cudaFreeAsync(flags, st);
+  TN_CUDA_TRY(le);
+  TN_CUDA_TRY(ce);
+  TN_CUDA_TRY(cudaStreamSynchronize(st));
+  if (f) { set_error("non-finite or zero bond spectrum in the truncation solve"); return TN_ENUMERIC; }
   return TN_OK;
 }
 

@@ -290,7 +290,11 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
     dw[o] = (float)w0.x; dw[c2 + o] = (float)w0.y;
     dw[2 * c2 + o] = (float)w1.x; dw[3 * c2 + o] = (float)w1.y;
   }
-  if (ok) {
+  if (a.s_out) {
+    for (int i = threadIdx.x; i < chi; i += blockDim.x)
+      a.s_out[(int64_t)edge * chi + i] = ok ? sig[i] / nrm : 0.0;
+  }
+  if (ok && a.msg) {
     float* m0 = a.msg + (int64_t)a.msg_vw[2 * edge] * 2 * c2;
     float* m1 = a.msg + (int64_t)a.msg_vw[2 * edge + 1] * 2 * c2;
     for (int idx = threadIdx.x; idx < chi * chi; idx += blockDim.x) {

@@ -1,0 +1,99 @@
+"""The standalone FP64 truncation solve against NumPy's SVD of the two-site matrix.
+
+For random env-weighted site matrices X_v[p, r, e], X_w[q, r', e] the gate
+exp(s i pi/4 Z Z) gives Theta[(p, r), (q, r')] = sum_e X_v[p,r,e] g(p,q) X_w[q,r',e]
+(Eq. 1's two-site gate, "The simple update procedure").  The solve only sees
+the open-p environments N_p = X_p^T conj(X_p) and must return the chi largest
+singular values of Theta (normalised) and per-p leg matrices D_p whose
+products rebuild the truncated Theta.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tnlib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_14887_gb300 import build
+    build.build()
+    import paper_2306_14887_gb300 as tn
+    return tn
+
+
+def make_case(chi, rows, n_edges, seed):
+    r = np.random.default_rng(seed)
+    xs = []
+    gram = np.zeros((n_edges, 2, 2, 2, chi, chi), dtype=np.float32)
+    for k in range(n_edges):
+        pair = []
+        for side in range(2):
+            x = (r.standard_normal((2, rows, chi)) + 1j * r.standard_normal((2, rows, chi)))
+            x *= np.exp(-0.35 * np.arange(chi))[None, None, :]   # decaying spectrum
+            pair.append(x)
+            for p in range(2):
+                n_p = x[p].T @ x[p].conj()
+                gram[k, side, p, 0] = n_p.real
+                gram[k, side, p, 1] = n_p.imag
+        xs.append(pair)
+    return xs, gram
+
+
+def theta_matrix(xv, xw, sign):
+    s = np.array([1.0, -1.0])
+    g = np.exp(sign * 1j * np.pi / 4 * np.outer(s, s))
+    rows = xv.shape[1]
+    th = np.zeros((2 * rows, 2 * rows), dtype=complex)
+    for p in range(2):
+        for q in range(2):
+            th[p * rows:(p + 1) * rows, q * rows:(q + 1) * rows] = g[p, q] * xv[p] @ xw[q].T
+    return th
+
+
+def run_solve(tn, gram, chi, sign, n_edges):
+    import torch
+    dev = torch.device("cuda")
+    g = torch.from_numpy(gram.reshape(-1)).to(dev)
+    d = torch.zeros_like(g)
+    s = torch.zeros(n_edges * chi, dtype=torch.float64, device=dev)
+    tn.truncation_solve(g.data_ptr(), d.data_ptr(), s.data_ptr(), n_edges, chi, sign,
+                        stream=torch.cuda.current_stream().cuda_stream)
+    return d.cpu().numpy().reshape(gram.shape), s.cpu().numpy().reshape(n_edges, chi)
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+@pytest.mark.parametrize("chi,rows", [(4, 6), (8, 12), (16, 20)])
+def test_solve_matches_numpy_svd(tnlib, chi, rows, sign):
+    n_edges = 5
+    xs, gram = make_case(chi, rows, n_edges, seed=chi + 7 * rows + (sign > 0))
+    dmat, s = run_solve(tnlib, gram, chi, sign, n_edges)
+    for k in range(n_edges):
+        xv, xw = xs[k]
+        th = theta_matrix(xv, xw, sign)
+        u, sv, vh = np.linalg.svd(th)
+        keep = sv[:chi] / np.linalg.norm(sv[:chi])
+        assert np.allclose(s[k], keep, atol=2e-5 * keep[0])
+        # rebuilt halves: left = X_v D_v, right = X_w D_w
+        dv = dmat[k, 0, :, 0] + 1j * dmat[k, 0, :, 1]
+        dw = dmat[k, 1, :, 0] + 1j * dmat[k, 1, :, 1]
+        left = np.concatenate([xv[p] @ dv[p] for p in range(2)], axis=0)
+        right = np.concatenate([xw[q] @ dw[q] for q in range(2)], axis=0)
+        trunc = (u[:, :chi] * sv[:chi]) @ vh[:chi] / np.linalg.norm(sv[:chi])
+        scale = np.abs(trunc).max()
+        assert np.abs(left @ right.T - trunc).max() < 1e-4 * scale
+        # the left half is orthogonal with weights S (the new message diag(S))
+        assert np.allclose(left.conj().T @ left, np.diag(keep), atol=1e-4)
+
+
+def test_solve_rejects_bad_arguments(tnlib):
+    with pytest.raises(tnlib.TNError) as ei:
+        tnlib.truncation_solve(0, 0, 0, 1, 8)
+    assert ei.value.status == -1
+    import torch
+    g = torch.zeros(8 * 64, device="cuda")
+    with pytest.raises(tnlib.TNError) as ei:
+        tnlib.truncation_solve(g.data_ptr(), g.data_ptr(), g.data_ptr(), 1, 300)
+    assert ei.value.status == -1
