@@ -222,6 +222,28 @@ tn_status tn_expect_z_all(tn_handle* h, double* out);
 tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int32_t n_edges,
                               int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream);
 
+/*
+ * tn_truncation_solve_noalloc — tn_truncation_solve for callers that cannot
+ * allocate device memory (a host application or serving runtime that owns the
+ * whole device pool, or a latency-bound loop that cannot afford the
+ * synchronisation cudaMalloc/cudaFree may imply).  The paper has no
+ * counterpart: this is a deployment variant.  Same arguments, layouts, results
+ * and errors as tn_truncation_solve; the caller still passes gram, dmat and
+ * s_out.  The FP64 workspace is one fixed 16 MiB device array inside the
+ * library (held by every GPU that loads it until the process exits), so a call
+ * needs n_edges * (12 (2 chi)^2 + 4) + 1 <= 2^21 doubles (for example up to 10
+ * edges at chi = 64, 42 at chi = 32); larger requests fail with TN_EINVAL and a
+ * message giving the limit.  No cudaMalloc, cudaFree or other allocating call
+ * is made.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call shares the one array, which keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.
+ */
+tn_status tn_truncation_solve_noalloc(const float* gram, float* dmat, double* s_out,
+                                      int32_t n_edges, int32_t chi, int32_t sign,
+                                      double svd_cutoff, void* cuda_stream);
+
 /* tn_get_stats — counters of the last evolution call. */
 tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
 

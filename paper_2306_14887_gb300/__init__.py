@@ -27,8 +27,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_bp_converge", "tn_expect", "tn_expect_z_all", "tn_get_stats", "tn_get_site",
            "tn_set_site", "tn_get_message", "tn_set_message", "tn_footprint",
            "tn_footprint_estimate", "tn_heavy_hex", "tn_clifford_reduce", "tn_profile_enable",
-           "tn_profile_read", "tn_profile_class_name", "tn_truncation_solve", "tn_last_error",
-           "tn_version"]
+           "tn_profile_read", "tn_profile_class_name", "tn_truncation_solve",
+           "tn_truncation_solve_noalloc", "tn_last_error", "tn_version"]
 
 
 class TNError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
         L.tn_profile_class_name.argtypes = [i32]
         L.tn_profile_class_name.restype = C.c_char_p
         L.tn_truncation_solve.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
+        L.tn_truncation_solve_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
         L.tn_last_error.restype = C.c_char_p
         L.tn_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -155,6 +156,15 @@ def truncation_solve(gram, dmat, s_out, n_edges, chi, sign=1, svd_cutoff=0.0, st
     _check(lib().tn_truncation_solve(C.c_void_p(gram), C.c_void_p(dmat), C.c_void_p(s_out),
                                      int(n_edges), int(chi), int(sign), float(svd_cutoff),
                                      C.c_void_p(stream)))
+
+
+def truncation_solve_noalloc(gram, dmat, s_out, n_edges, chi, sign=1, svd_cutoff=0.0, stream=0):
+    """tn_truncation_solve without device allocation: for callers whose device
+    memory is owned by someone else; workspace is a fixed 16 MiB array in the
+    library (see include/tnbp.h for the size limit and the sharing rules)."""
+    _check(lib().tn_truncation_solve_noalloc(C.c_void_p(gram), C.c_void_p(dmat),
+                                             C.c_void_p(s_out), int(n_edges), int(chi),
+                                             int(sign), float(svd_cutoff), C.c_void_p(stream)))
 
 
 def _graph_struct(n, edges, colours):
