@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--chi", type=int, default=64)
     p.add_argument("--prec", default="fp32")
+    p.add_argument("--solve", default="auto", choices=["auto", "shared", "fp64"])
     p.add_argument("--theta", type=float, default=None)
     p.add_argument("--presteps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -245,7 +246,7 @@ def run_ours(args, rank, world, local):
     theta = theta_for(rank, args)
     n, edges, cols = eagle()
     stream = torch.cuda.Stream()
-    s = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream)
+    s = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream, solve=args.solve)
     s.apply_floquet(theta, presteps)
     for _ in range(args.warmup):
         s.apply_floquet(theta, 1)
@@ -291,7 +292,7 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         stream.synchronize()
         t0 = time.perf_counter()
-        s2 = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream)
+        s2 = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream, solve=args.solve)
         zs = []
         for _ in range(args.steps):
             s2.apply_floquet(theta, 1)
@@ -314,7 +315,7 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32"}.get(args.prec, args.prec) + "+f64solve",
         "data": "synthetic (initial state |0..0>, theta_h from the uniform [0, pi/2] grid)",
-        "config": {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, "
+        "config": {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, solve={args.solve}, "
                                f"theta_h={theta:.4f}, saturated after {presteps} steps",
                    "qubits": int(n), "edges": int(len(edges)), "chi": chi,
                    "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (

@@ -95,7 +95,23 @@ typedef struct {
   double svd_cutoff;    /* singular values below svd_cutoff * sigma_1 are dropped;
                            <= 0 selects the precision's default */
   uint64_t seed;        /* reserved (the method draws no random numbers) */
+  int32_t solve;        /* truncation solve: TN_SOLVE_AUTO, TN_SOLVE_FP64 or TN_SOLVE_SHARED */
 } tn_config;
+
+/* Truncation solve variants.
+ * TN_SOLVE_FP64: Hermitian Jacobi eigen-solves in FP64 on global-memory
+ *   workspaces (all solve arithmetic FP64; slow on GB300, whose FP64 rate is
+ *   about 1/64 of FP32).
+ * TN_SOLVE_SHARED: FP64 pivoted Cholesky of the Gram blocks, then one-sided
+ *   Jacobi of the 2chi x 2chi bond matrix in shared memory with FP32 rotations
+ *   and the spectrum accumulated in FP64 (chi <= 64; larger chi fall back to
+ *   TN_SOLVE_FP64).  Singular values to about 2e-6 relative; end to end about
+ *   1e-5 in <Z> against the FP64 oracle.
+ * TN_SOLVE_AUTO: TN_SOLVE_FP64 when prec is TN_FP32 (the plain path that must
+ *   match the FP64 oracle to 1e-6 in <Z>), TN_SOLVE_SHARED otherwise. */
+#define TN_SOLVE_AUTO 0
+#define TN_SOLVE_FP64 1
+#define TN_SOLVE_SHARED 2
 
 /* Device allocator callbacks.  alloc returns device memory of at least `bytes`
  * bytes usable on `stream` (NULL on failure); free releases it. */
@@ -221,6 +237,13 @@ tn_status tn_expect_z_all(tn_handle* h, double* out);
  */
 tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int32_t n_edges,
                               int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream);
+
+/* tn_truncation_solve_ex — tn_truncation_solve with the solve variant chosen:
+ * TN_SOLVE_FP64 (what tn_truncation_solve runs; also for TN_SOLVE_AUTO) or
+ * TN_SOLVE_SHARED (chi <= 64, TN_EUNSUPPORTED otherwise). */
+tn_status tn_truncation_solve_ex(const float* gram, float* dmat, double* s_out, int32_t n_edges,
+                                 int32_t chi, int32_t sign, double svd_cutoff, int32_t solve,
+                                 void* cuda_stream);
 
 /*
  * tn_truncation_solve_noalloc — tn_truncation_solve for callers that cannot

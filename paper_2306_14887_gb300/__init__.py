@@ -21,6 +21,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ENOTCONVERGED",
           -4: "TN_ENUMERIC", -5: "TN_ETIMEOUT", -6: "TN_ECUDA", -7: "TN_EAGAIN",
           -8: "TN_EUNSUPPORTED"}
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
+SOLVES = {"auto": 0, "fp64": 1, "shared": 2}
 
 #: every symbol include/tnbp.h declares
 EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dagger",
@@ -28,7 +29,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_set_site", "tn_get_message", "tn_set_message", "tn_footprint",
            "tn_footprint_estimate", "tn_heavy_hex", "tn_clifford_reduce", "tn_profile_enable",
            "tn_profile_read", "tn_profile_class_name", "tn_truncation_solve",
-           "tn_truncation_solve_noalloc", "tn_last_error", "tn_version"]
+           "tn_truncation_solve_noalloc", "tn_truncation_solve_ex", "tn_last_error",
+           "tn_version"]
 
 
 class TNError(RuntimeError):
@@ -45,7 +47,8 @@ class tn_graph(C.Structure):
 
 class tn_config(C.Structure):
     _fields_ = [("chi", C.c_int32), ("prec", C.c_int32), ("bp_tol", C.c_double),
-                ("bp_max_iters", C.c_int32), ("svd_cutoff", C.c_double), ("seed", C.c_uint64)]
+                ("bp_max_iters", C.c_int32), ("svd_cutoff", C.c_double), ("seed", C.c_uint64),
+                ("solve", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -111,6 +114,7 @@ def lib():
         L.tn_profile_class_name.restype = C.c_char_p
         L.tn_truncation_solve.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
         L.tn_truncation_solve_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
+        L.tn_truncation_solve_ex.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, i32, vp]
         L.tn_last_error.restype = C.c_char_p
         L.tn_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -151,11 +155,12 @@ def clifford_reduce(n, edges, ops, sign=1, max_steps=32, colours=None):
     return a.value, b.value, c.value
 
 
-def truncation_solve(gram, dmat, s_out, n_edges, chi, sign=1, svd_cutoff=0.0, stream=0):
-    """Standalone FP64 truncation solve on device buffers (raw pointers as ints)."""
-    _check(lib().tn_truncation_solve(C.c_void_p(gram), C.c_void_p(dmat), C.c_void_p(s_out),
-                                     int(n_edges), int(chi), int(sign), float(svd_cutoff),
-                                     C.c_void_p(stream)))
+def truncation_solve(gram, dmat, s_out, n_edges, chi, sign=1, svd_cutoff=0.0, stream=0,
+                     solve="fp64"):
+    """Standalone truncation solve on device buffers (raw pointers as ints)."""
+    _check(lib().tn_truncation_solve_ex(C.c_void_p(gram), C.c_void_p(dmat), C.c_void_p(s_out),
+                                        int(n_edges), int(chi), int(sign), float(svd_cutoff),
+                                        SOLVES[solve], C.c_void_p(stream)))
 
 
 def truncation_solve_noalloc(gram, dmat, s_out, n_edges, chi, sign=1, svd_cutoff=0.0, stream=0):
@@ -184,8 +189,9 @@ def _graph_struct(n, edges, colours):
     return g, keep
 
 
-def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff):
+def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve="auto"):
     c = tn_config()
+    c.solve = SOLVES[solve] if isinstance(solve, str) else int(solve)
     c.chi = int(chi)
     c.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     c.bp_tol = float(bp_tol)
@@ -207,7 +213,8 @@ class TNState:
     """A tensor-network state on one graph, resident on the current CUDA device."""
 
     def __init__(self, n, edges, colours=None, chi=8, prec="fp32", bp_tol=1e-10,
-                 bp_max_iters=1000, svd_cutoff=0.0, stream=None, torch_allocator=True):
+                 bp_max_iters=1000, svd_cutoff=0.0, stream=None, torch_allocator=True,
+                 solve="auto"):
         import torch
         self._torch = torch
         L = lib()
@@ -215,7 +222,7 @@ class TNState:
         self.edges = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
         self.chi = int(chi)
         g, self._keep = _graph_struct(n, edges, colours)
-        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff)
+        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve)
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream

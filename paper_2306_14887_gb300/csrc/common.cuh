@@ -97,5 +97,8 @@ struct SolveArgs {
 };
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s);
 size_t solve_work_doubles(int chi);
+// Shared-memory solve with FP32 rotations (solve32.cu), chi <= 64.
+bool solve32_supported(int chi);
+cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t s);
 
 }  // namespace tnbp

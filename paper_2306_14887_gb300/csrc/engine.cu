@@ -648,6 +648,13 @@ double default_svd_cut(const tn_handle* h) {
                                                                                        : 1e-4;
 }
 
+bool use_shared_solve(const tn_handle* h) {
+  const int sv = h->cfg.solve == TN_SOLVE_AUTO
+                     ? (h->cfg.prec == TN_FP32 ? TN_SOLVE_FP64 : TN_SOLVE_SHARED)
+                     : h->cfg.solve;
+  return sv == TN_SOLVE_SHARED && solve32_supported(h->chi);
+}
+
 // Residual below which FP32-stored messages can no longer improve.
 double precision_floor(const tn_handle* h) {
   switch (h->cfg.prec) {
@@ -677,7 +684,12 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   a.s_out = nullptr;
   {
     const int pi = prof_begin(h, P_SOLVE);
-    TN_CUDA_TRY(launch_solve(a, h->stream));
+    if (use_shared_solve(h)) {
+      a.max_sweeps = 20;
+      TN_CUDA_TRY(launch_solve32(a, h->stream));
+    } else {
+      TN_CUDA_TRY(launch_solve(a, h->stream));
+    }
     const double n = 2.0 * h->chi;
     prof_end(h, pi, 40.0 * n * n * n * a.n_edges, 4.0 * 16.0 * h->chi * h->chi * a.n_edges);
   }
@@ -706,9 +718,11 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
 tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, double* res) {
   const int nmsg = 2 * (int)h->g.eu.size();
   // Messages are stored in FP32: once the residual is down at the rounding
-  // floor of the arithmetic it stops decreasing.  Below `floor`, a sweep that
-  // fails to halve the residual of three sweeps before ends the iteration as
-  // converged (the FP64 tolerance cannot be met by FP32 messages).
+  // floor of the arithmetic it stops decreasing and only fluctuates.  Below
+  // `floor`, a sweep whose residual is not below 0.98 of the previous one
+  // (the floor's signature; slow but steady convergence keeps going), or a
+  // residual under floor / 8, ends the iteration as converged: the FP64
+  // tolerance cannot be met by FP32 messages.
   const double floor = precision_floor(h);
   double r = INFINITY;
   std::vector<double> hist;
@@ -732,7 +746,7 @@ tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, 
     if (r < tol) break;
     hist.push_back(r);
     const size_t k = hist.size();
-    if (r < floor && k >= 4 && r > 0.5 * hist[k - 4]) {
+    if (r < floor && (r < floor / 8 || (k >= 2 && r >= 0.98 * hist[k - 2]))) {
       stagnated = true;
       break;
     }
@@ -870,6 +884,10 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   if (cfg->chi < 1 || cfg->chi > 256) { set_error("chi must be in 1..256"); return TN_EINVAL; }
   if (cfg->prec < TN_FP32 || cfg->prec > TN_TF32X3) { set_error("unknown precision"); return TN_EINVAL; }
   if (cfg->prec != TN_FP32) { set_error("precision mode not built yet"); return TN_EUNSUPPORTED; }
+  if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64) {
+    set_error("unknown truncation solve");
+    return TN_EINVAL;
+  }
   if (!(cfg->bp_tol > 0) || cfg->bp_max_iters < 1) {
     set_error("bp_tol must be > 0 and bp_max_iters >= 1");
     return TN_EINVAL;
@@ -1171,6 +1189,21 @@ tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t me
 
 tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int32_t n_edges,
                               int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream) {
+  return tn_truncation_solve_ex(gram, dmat, s_out, n_edges, chi, sign, svd_cutoff, TN_SOLVE_FP64,
+                                cuda_stream);
+}
+
+tn_status tn_truncation_solve_ex(const float* gram, float* dmat, double* s_out, int32_t n_edges,
+                                 int32_t chi, int32_t sign, double svd_cutoff, int32_t solve,
+                                 void* cuda_stream) {
+  if (solve != TN_SOLVE_AUTO && solve != TN_SOLVE_SHARED && solve != TN_SOLVE_FP64) {
+    set_error("unknown truncation solve");
+    return TN_EINVAL;
+  }
+  if (solve == TN_SOLVE_SHARED && !solve32_supported(chi)) {
+    set_error("the shared-memory solve supports chi <= 64");
+    return TN_EUNSUPPORTED;
+  }
   if (!gram || !dmat || !s_out) { set_error("null argument"); return TN_EINVAL; }
   if (n_edges < 1 || chi < 1 || 2 * chi > 512 || (sign != 1 && sign != -1)) {
     set_error("n_edges >= 1, 1 <= chi <= 256 and sign = +-1 required");
@@ -1199,7 +1232,13 @@ tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int
   a.stats = (double*)stats;
   a.flags = (int*)flags;
   a.max_sweeps = 30;
-  cudaError_t le = launch_solve(a, st);
+  cudaError_t le;
+  if (solve == TN_SOLVE_SHARED) {
+    a.max_sweeps = 20;
+    le = launch_solve32(a, st);
+  } else {
+    le = launch_solve(a, st);
+  }
   int f = 0;
   cudaError_t ce = cudaMemcpyAsync(&f, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(work, st);

@@ -1,0 +1,562 @@
+// Shared-memory truncation solve with FP32 rotations (chi <= 64).
+//
+// Same inputs and outputs as the FP64 solve in solve.cu (open-p environments
+// of both sides of each gate edge in; per-p leg matrices D, the new bond
+// spectrum and the gate-edge messages out), organised so that the O(chi^3)
+// iterative part (the one-sided Jacobi sweeps) runs from shared memory on the
+// FP32 pipes.  The Gram factorisations, norms, the spectrum and its
+// normalisation are FP64.
+//
+// The gate exp(s i pi/4 ZZ) is split on the projectors of v's physical index:
+// exp(s i pi/4 ZZ) = sum_p |p><p| (x) B_p, B_p = exp(s i pi/4 s_p Z), s_0 = +1,
+// s_1 = -1 (Eq. 1's two-site gate).  The gate-split matrix of the v side,
+// Xv[(p', r), (e, k)] = delta_{k p'} X_v[p', r, e], then has the block-diagonal
+// Gram matrix G_v = diag(conj N_0, conj N_1); on the w side
+// G_w[(e,k), (e',k')] = sum_q conj(b_k(q)) b_k'(q) conj(N_q^w)[e, e'] with
+// b_k(q) = exp(s i pi/4 s_k s_q).  Steps per edge (one CTA):
+//   1. pivoted Cholesky (FP64) of the two chi x chi blocks of G_v and of G_w
+//      (2chi): P^T G P = L L^H, so G = R^H R with R = L^H P^T;
+//   2. K^T = R_w R_v^T (the bond matrix K = R_v R_w^T, transposed);
+//   3. one-sided Jacobi on the columns of K (rows of K^T) until every pair is
+//      orthogonal to FP32 precision: K V = U diag(sigma), with no squaring of
+//      the condition number;
+//   4. keep the chi largest sigma (above svd_cut * sigma_1), S = sigma/||sigma||;
+//   5. C_v = R_v^+ U sqrt(S) (any z with R_v z = u serves: solutions differ by
+//      null(R_v) = null(Xv), invisible in Xv z), C_w = R_v^T conj(U) / sqrt(sigma ||sigma||);
+//   6. D_v[p] = C_v[block p], D_w[q] = sum_k b_k(q) C_w[block k]; both gate-edge
+//      messages <- diag(S).
+#include <math.h>
+
+#include "common.cuh"
+#include "tnbp.h"
+
+namespace tnbp {
+namespace {
+
+constexpr int kThreads = 512;
+
+__device__ __forceinline__ int64_t solve_work_doubles_dev(int chi) {
+  return (int64_t)12 * (2 * chi) * (2 * chi);
+}
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxChi = 64;
+constexpr float kOrthTol = 2e-6f;
+constexpr double kAbsTol = 1e-12;
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconjf(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+struct zd { double x, y; };
+__device__ __forceinline__ zd zmul(zd a, zd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ zd zconj(zd a) { return {a.x, -a.y}; }
+
+// FP64 pivoted Cholesky of the Hermitian PSD m x m matrix A (row stride ld,
+// full storage) in place: afterwards A's lower triangle holds L with
+// P^T A P = L L^H, perm[t] = original index of pivot t, and *rank the number of
+// pivots above rel_tol * (largest initial diagonal); everything outside the
+// first `rank` columns of the lower triangle is zeroed.  The trailing update
+// keeps the full Hermitian block current, so each pivot's row and column
+// exchange reads current values.  A may live in shared or global memory.  colk: m complex doubles of shared scratch holding
+// the current column of L for the trailing update.
+__device__ void pivoted_cholesky64(zd* A, int m, int ld, int* perm, double rel_tol, int* rank,
+                                   double* red_v, int* red_i, double* dmax0, zd* colk) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < m; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  int r = m;
+  for (int k = 0; k < m; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < m; i += blockDim.x) {
+      const double d = A[(int64_t)i * ld + i].x;
+      if (d > best) { best = d; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = red_v[0];
+      int ii = red_i[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (red_v[w] > b || (red_v[w] == b && red_i[w] < ii)) { b = red_v[w]; ii = red_i[w]; }
+      red_v[0] = b;
+      red_i[0] = ii;
+      if (k == 0) *dmax0 = b > 0.0 ? b : 0.0;
+    }
+    __syncthreads();
+    const double pv = red_v[0];
+    const int piv = red_i[0];
+    const double d0 = *dmax0;
+    __syncthreads();
+    if (!(d0 > 0.0) || !(pv > rel_tol * d0)) { r = k; break; }
+    if (piv != k) {
+      for (int j = tid; j < m; j += blockDim.x) {
+        const zd t = A[(int64_t)k * ld + j];
+        A[(int64_t)k * ld + j] = A[(int64_t)piv * ld + j];
+        A[(int64_t)piv * ld + j] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += blockDim.x) {
+        const zd t = A[(int64_t)i * ld + k];
+        A[(int64_t)i * ld + k] = A[(int64_t)i * ld + piv];
+        A[(int64_t)i * ld + piv] = t;
+      }
+      if (tid == 0) { const int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t; }
+      __syncthreads();
+    }
+    const double d = sqrt(A[(int64_t)k * ld + k].x);
+    const double inv = 1.0 / d;
+    __syncthreads();
+    for (int i = k + 1 + tid; i < m; i += blockDim.x) {
+      const zd a = A[(int64_t)i * ld + k];
+      const zd l = {a.x * inv, a.y * inv};
+      A[(int64_t)i * ld + k] = l;
+      colk[i] = l;
+    }
+    __syncthreads();
+    if (tid == 0) A[(int64_t)k * ld + k] = {d, 0.0};
+    const int rem = m - k - 1;
+    for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+      const zd p = zmul(colk[i], zconj(colk[j]));
+      zd a = A[(int64_t)i * ld + j];
+      a.x -= p.x;
+      a.y -= p.y;
+      A[(int64_t)i * ld + j] = a;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    if (j > i || j >= r) A[(int64_t)i * ld + j] = {0.0, 0.0};
+  }
+  if (tid == 0) *rank = r;
+  __syncthreads();
+}
+
+struct Smem {
+  float2* X;       // n x n: G_w -> L_w -> K^T -> rotated columns of K
+  float2* Lv;      // 2 blocks chi x chi: L_0, L_1
+  int* perm_w;     // n
+  int* perm_v;     // 2 chi
+  int* src;        // n: K^T gather map
+  int* order;      // n: rows by decreasing norm
+  int* rank;       // 4
+  int* red_i;      // 32
+  float* red_v;    // 32
+  float* dmax0;    // 4
+  int* counter;    // 4
+  double* sig;     // n
+  double* scal;    // 4
+  double* red_d;   // 32
+  zd* colk;        // n
+};
+
+__device__ Smem carve(unsigned char* base, int chi) {
+  const int n = 2 * chi;
+  Smem s;
+  unsigned char* p = base;
+  s.X = reinterpret_cast<float2*>(p); p += sizeof(float2) * n * n;
+  s.Lv = reinterpret_cast<float2*>(p); p += sizeof(float2) * 2 * chi * chi;
+  s.sig = reinterpret_cast<double*>(p); p += sizeof(double) * n;
+  s.scal = reinterpret_cast<double*>(p); p += sizeof(double) * 4;
+  s.red_d = reinterpret_cast<double*>(p); p += sizeof(double) * 32;
+  s.colk = reinterpret_cast<zd*>(p); p += sizeof(zd) * n;
+  s.perm_w = reinterpret_cast<int*>(p); p += sizeof(int) * n;
+  s.perm_v = reinterpret_cast<int*>(p); p += sizeof(int) * 2 * chi;
+  s.src = reinterpret_cast<int*>(p); p += sizeof(int) * n;
+  s.order = reinterpret_cast<int*>(p); p += sizeof(int) * n;
+  s.rank = reinterpret_cast<int*>(p); p += sizeof(int) * 4;
+  s.red_i = reinterpret_cast<int*>(p); p += sizeof(int) * 32;
+  s.red_v = reinterpret_cast<float*>(p); p += sizeof(float) * 32;
+  s.dmax0 = reinterpret_cast<float*>(p); p += sizeof(float) * 4;
+  s.counter = reinterpret_cast<int*>(p); p += sizeof(int) * 4;
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int chi = a.chi, n = 2 * chi;
+  const int64_t c2 = (int64_t)chi * chi;
+  const int edge = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  Smem s = carve(smem_raw, chi);
+  float2* X = s.X;
+  const float* gv = a.gram + (int64_t)edge * 8 * c2;
+  const float* gw = gv + 4 * c2;
+  const float sg = (float)a.sign;
+
+  // 1. Gram matrices in FP64.  G_v blocks conj(N_p^v) in shared memory (they
+  //    fit in the space X takes later); G_w from conj(N_q^w) in this edge's
+  //    global workspace (L2-resident).
+  zd* Gv64 = reinterpret_cast<zd*>(X);                    // 2 chi^2 zd == n^2 float2
+  zd* Gw64 = reinterpret_cast<zd*>(a.work + (int64_t)edge * solve_work_doubles_dev(chi));
+  for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
+    const int p = idx / (chi * chi), o = idx % (chi * chi);
+    Gv64[idx] = {(double)gv[p * 2 * c2 + o], -(double)gv[p * 2 * c2 + c2 + o]};
+  }
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    const int ki = i / chi, ei = i % chi, kj = j / chi, ej = j % chi;
+    const int64_t o = (int64_t)ei * chi + ej;
+    const zd g0 = {(double)gw[o], -(double)gw[c2 + o]};
+    const zd g1 = {(double)gw[2 * c2 + o], -(double)gw[3 * c2 + o]};
+    zd v;
+    if (ki == kj) {
+      v = {g0.x + g1.x, g0.y + g1.y};
+    } else {
+      // conj(b_ki(q)) b_kj(q) = exp(s i pi/4 (s_kj - s_ki) s_q): (0,1) -> -s i s_q,
+      // (1,0) -> +s i s_q, so the block is -+ s i (G_0 - G_1)
+      const zd d = {g0.x - g1.x, g0.y - g1.y};
+      const double f = (ki == 0) ? -(double)sg : (double)sg;
+      v = {-f * d.y, f * d.x};
+    }
+    Gw64[idx] = v;
+  }
+  __syncthreads();
+  const double ctol = 1e-13;
+  double* dmax0d = s.scal + 3;
+  pivoted_cholesky64(Gv64, chi, chi, s.perm_v, ctol, &s.rank[0], s.red_d, s.red_i, dmax0d, s.colk);
+  pivoted_cholesky64(Gv64 + chi * chi, chi, chi, s.perm_v + chi, ctol, &s.rank[1], s.red_d,
+                     s.red_i, dmax0d, s.colk);
+  for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x)
+    s.Lv[idx] = make_float2((float)Gv64[idx].x, (float)Gv64[idx].y);
+  __syncthreads();
+  pivoted_cholesky64(Gw64, n, n, s.perm_w, ctol, &s.rank[2], s.red_d, s.red_i, dmax0d, s.colk);
+
+  // 2. K^T = R_w R_v^T.  First X[j][t] = conj(L_w[t][j]) (FP32), so that row j
+  //    of X holds R_w[j][perm_w[t]] at column t.  Then with c = perm_b[t'] (block b):
+  //    K^T[j][(b, i)] = sum_t' X[j][pinv_w(b chi + perm_b[t'])] conj(L_b[t'][i]).
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int j = idx / n, t = idx % n;
+    const zd l = Gw64[(int64_t)t * n + j];
+    X[idx] = make_float2((float)l.x, (float)-l.y);
+  }
+  // src[(b, t')] = pinv_w(b chi + perm_b[t'])
+  for (int t = tid; t < n; t += blockDim.x) s.src[s.perm_w[t]] = -1 - t;  // temp: pinv_w
+  __syncthreads();
+  for (int bt = tid; bt < n; bt += blockDim.x) {
+    const int b = bt / chi, tp = bt % chi;
+    const int c = b * chi + s.perm_v[b * chi + tp];
+    s.order[bt] = -1 - s.src[c];  // pinv_w(c), staged in order[]
+  }
+  __syncthreads();
+  for (int bt = tid; bt < n; bt += blockDim.x) s.src[bt] = s.order[bt];
+  __syncthreads();
+  const int npl = n / 32 > 0 ? (n + 31) / 32 : 1;  // values per lane (<= 4)
+  for (int j = warp; j < n; j += kWarps) {
+    float2 y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int bt = u * 32 + lane;
+      y[u] = (u < npl && bt < n) ? X[j * n + s.src[bt]] : make_float2(0.f, 0.f);
+    }
+    float2 out[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[u] = make_float2(0.f, 0.f);
+    for (int bt = 0; bt < n; ++bt) {
+      const float2 yv = shfl2(y[bt >> 5], bt & 31);
+      const int b = bt / chi, tp = bt % chi;
+      const float2* Lb = s.Lv + b * chi * chi;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int o = u * 32 + lane;  // output (b, i) = o
+        if (u < npl && o < n && o / chi == b) {
+          const int i = o % chi;
+          if (i <= tp) {
+            const float2 p = cmulf(yv, cconjf(Lb[tp * chi + i]));
+            out[u].x += p.x;
+            out[u].y += p.y;
+          }
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int o = u * 32 + lane;
+      if (u < npl && o < n) X[j * n + o] = out[u];
+    }
+  }
+  __syncthreads();
+
+  // 3. One-sided Jacobi on the rows of X (columns of K), round-robin pairs.
+  //    ||K||_F^2 (invariant under the rotations) sets an absolute floor: a pair
+  //    whose overlap is below kAbsTol ||K||_F^2 cannot move any singular value
+  //    above the truncation cut, and rotating rounding noise would never stop.
+  {
+    double acc = 0.0;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const float2 v = X[idx];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) s.red_d[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += s.red_d[w];
+      s.scal[2] = t;
+    }
+    __syncthreads();
+  }
+  const float abs_floor = (float)(kAbsTol * s.scal[2]);
+  const int half = n / 2;
+  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    if (tid == 0) s.counter[0] = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int k = warp; k < half; k += kWarps) {
+        int p, q;
+        if (k == 0) { p = r; q = n - 1; }
+        else { p = (r + k) % (n - 1); q = (r - k + (n - 1)) % (n - 1); }
+        float2 xp[4], xq[4];
+        float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = u * 32 + lane;
+          if (u < npl && c < n) {
+            xp[u] = X[p * n + c];
+            xq[u] = X[q * n + c];
+          } else {
+            xp[u] = xq[u] = make_float2(0.f, 0.f);
+          }
+          al += xp[u].x * xp[u].x + xp[u].y * xp[u].y;
+          be += xq[u].x * xq[u].x + xq[u].y * xq[u].y;
+          // gamma = sum conj(xp) xq
+          gr += xp[u].x * xq[u].x + xp[u].y * xq[u].y;
+          gi += xp[u].x * xq[u].y - xp[u].y * xq[u].x;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gi = warp_sum(gi);
+        const float gm = sqrtf(gr * gr + gi * gi);
+        // pairs already orthogonal to FP32 precision are left alone; a sweep
+        // that rotates no pair ends the iteration
+        if (gm > kOrthTol * sqrtf(al * be) && gm > abs_floor && gm > 0.f) {
+          const float2 ph = make_float2(gr / gm, -gi / gm);  // e^{-i phi}, gamma = |g| e^{i phi}
+          const float tau = (be - al) / (2.f * gm);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          // exactly rounded: an approximate reciprocal square root makes every
+          // rotation slightly non-unitary and the column norms drift
+          const float cs = 1.f / sqrtf(1.f + t * t);
+          const float sn = t * cs;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = u * 32 + lane;
+            if (u < npl && c < n) {
+              const float2 pq = cmulf(ph, xq[u]);
+              X[p * n + c] = make_float2(cs * xp[u].x - sn * pq.x, cs * xp[u].y - sn * pq.y);
+              X[q * n + c] = make_float2(sn * xp[u].x + cs * pq.x, sn * xp[u].y + cs * pq.y);
+            }
+          }
+          if (lane == 0) atomicAdd(s.counter, 1);
+        }
+      }
+      __syncthreads();
+    }
+    if (s.counter[0] == 0) break;
+    __syncthreads();
+  }
+
+  // 4. sigma_j = ||row j|| (FP64), order by decreasing sigma, truncate, normalise.
+  for (int j = warp; j < n; j += kWarps) {
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) {
+      const float2 v = X[j * n + c];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) s.sig[j] = sqrt(acc);
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double si = s.sig[i];
+    int rk = 0;
+    for (int j = 0; j < n; ++j) {
+      const double sj = s.sig[j];
+      rk += (sj > si) || (sj == si && j < i);
+    }
+    s.order[rk] = i;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0, kept = 0.0;
+    for (int i = 0; i < n; ++i) tot += s.sig[i] * s.sig[i];
+    const double s0 = s.sig[s.order[0]];
+    int nk = 0;
+    for (int m = 0; m < chi; ++m) {
+      const double v = s.sig[s.order[m]];
+      if (v > 0.0 && v > a.svd_cut * s0) { kept += v * v; ++nk; }
+    }
+    s.scal[0] = sqrt(kept);
+    s.scal[1] = nk;
+    double* st = a.stats + 4 * edge;
+    st[0] = tot > 0.0 ? (tot - kept) / tot : 0.0;
+    st[1] = nk;
+    st[2] = s0;
+    st[3] = 0.0;
+    if (!(kept > 0.0) || !isfinite(kept)) atomicOr(a.flags, 1);
+  }
+  __syncthreads();
+  const double nrm = s.scal[0];
+  const int nk = (int)s.scal[1];
+  const bool ok = nrm > 0.0 && isfinite(nrm);
+
+  // 5-6. One warp per kept column m: u = row_j / sigma (length n, index (b, i)).
+  float* dv = a.dmat + (int64_t)edge * 8 * c2;
+  float* dw = dv + 4 * c2;
+  const float c45 = 0.70710678118654752f;
+  for (int m = warp; m < chi; m += kWarps) {
+    const bool keep = ok && m < nk;
+    const int j = s.order[m];
+    const double sgm = s.sig[j];
+    const float fv = keep ? (float)sqrt(sgm / nrm) : 0.f;        // sqrt(S_m)
+    const float fw = keep ? (float)(1.0 / sqrt(sgm * nrm)) : 0.f;  // 1/sqrt(sigma ||sigma||)
+    const float inv_s = keep ? (float)(1.0 / sgm) : 0.f;
+    for (int b = 0; b < 2; ++b) {
+      const float2* Lb = s.Lv + b * chi * chi;
+      const int rb = s.rank[b];
+      const int* pb = s.perm_v + b * chi;
+      // u block b, lane owns entries i = lane, lane + 32
+      float2 u[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = h * 32 + lane;
+        u[h] = (keep && i < chi) ? X[j * n + b * chi + i] : make_float2(0.f, 0.f);
+        u[h].x *= inv_s;
+        u[h].y *= inv_s;
+      }
+      // C_v block b: solve L_b^H w = u (back substitution over t < rank), z[perm[t]] = w[t]
+      float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      for (int t = rb - 1; t >= 0; --t) {
+        // w[t] = (u[t] - sum_{t2 > t} conj(L[t2][t]) w[t2]) / L[t][t]
+        float2 part = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int t2 = h * 32 + lane;
+          if (t2 > t && t2 < rb) {
+            const float2 pr = cmulf(cconjf(Lb[t2 * chi + t]), w[h]);
+            part.x += pr.x;
+            part.y += pr.y;
+          }
+        }
+        part.x = warp_sum(part.x);
+        part.y = warp_sum(part.y);
+        const float2 ut = shfl2(u[t >> 5], t & 31);
+        const float d = Lb[t * chi + t].x;
+        const float2 wt = make_float2((ut.x - part.x) / d, (ut.y - part.y) / d);
+        if ((t >> 5) == 0 && lane == (t & 31)) w[0] = wt;
+        if ((t >> 5) == 1 && lane == (t & 31)) w[1] = wt;
+      }
+      // D_v[p = b][e][m] = z[e] * sqrt(S_m), e = perm_b[t]
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = h * 32 + lane;
+        if (t < chi) {
+          const int e = pb[t];
+          const float2 z = (t < rb) ? make_float2(w[h].x * fv, w[h].y * fv) : make_float2(0.f, 0.f);
+          dv[b * 2 * c2 + (int64_t)e * chi + m] = z.x;
+          dv[b * 2 * c2 + c2 + (int64_t)e * chi + m] = z.y;
+        }
+      }
+      // C_w block b: y[t] = sum_{i <= t} L_b[t][i] u[i] (lower-triangular matvec),
+      // C_w[(b, perm_b[t])][m] = conj(y[t]) * fw.  D_w[q] = sum_k b_k(q) C_w[block k].
+      float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      for (int i = 0; i < chi; ++i) {
+        const float2 ui = shfl2(u[i >> 5], i & 31);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int t = h * 32 + lane;
+          if (t < chi && i <= t) {
+            const float2 pr = cmulf(Lb[t * chi + i], ui);
+            y[h].x += pr.x;
+            y[h].y += pr.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = h * 32 + lane;
+        if (t < chi) {
+          const int e = pb[t];
+          const float2 cw = make_float2(y[h].x * fw, -y[h].y * fw);
+          // b_b(q) = exp(s i pi/4 s_b s_q): q = 0 -> exp(s i pi/4 s_b), q = 1 -> its conjugate
+          const float sb = (b == 0) ? 1.f : -1.f;
+          const float2 b0 = make_float2(c45, sg * sb * c45);
+          const float2 b1 = make_float2(c45, -sg * sb * c45);
+          const float2 v0 = cmulf(b0, cw), v1 = cmulf(b1, cw);
+          float* d0 = dw + (int64_t)e * chi + m;
+          float* d1 = dw + 2 * c2 + (int64_t)e * chi + m;
+          if (b == 0) {
+            d0[0] = v0.x; d0[c2] = v0.y;
+            d1[0] = v1.x; d1[c2] = v1.y;
+          } else {
+            d0[0] += v0.x; d0[c2] += v0.y;
+            d1[0] += v1.x; d1[c2] += v1.y;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (a.s_out) {
+    for (int m = tid; m < chi; m += blockDim.x)
+      a.s_out[(int64_t)edge * chi + m] = (ok && m < nk) ? s.sig[s.order[m]] / nrm : 0.0;
+  }
+  if (ok && a.msg) {
+    float* m0 = a.msg + (int64_t)a.msg_vw[2 * edge] * 2 * c2;
+    float* m1 = a.msg + (int64_t)a.msg_vw[2 * edge + 1] * 2 * c2;
+    for (int idx = tid; idx < chi * chi; idx += blockDim.x) {
+      const int i = idx / chi, j = idx % chi;
+      const float val = (i == j && i < nk) ? (float)(s.sig[s.order[i]] / nrm) : 0.f;
+      m0[idx] = val; m0[c2 + idx] = 0.f;
+      m1[idx] = val; m1[c2 + idx] = 0.f;
+    }
+  }
+}
+
+size_t smem_bytes(int chi) {
+  const int n = 2 * chi;
+  return sizeof(float2) * (size_t)n * n + sizeof(float2) * 2 * chi * chi + sizeof(double) * (n + 4 + 32) +
+         sizeof(double) * 2 * n +
+         sizeof(int) * (n + 2 * chi + n + n + 4 + 32) + sizeof(float) * (32 + 4) + sizeof(int) * 4 + 64;
+}
+
+}  // namespace
+
+bool solve32_supported(int chi) { return chi >= 1 && chi <= kMaxChi; }
+
+cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t st) {
+  if (a.n_edges <= 0) return cudaSuccess;
+  if (!solve32_supported(a.chi)) return cudaErrorInvalidValue;
+  const size_t sm = smem_bytes(a.chi);
+  cudaError_t e = cudaFuncSetAttribute(solve32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  solve32_kernel<<<a.n_edges, kThreads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tnbp

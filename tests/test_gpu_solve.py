@@ -53,27 +53,30 @@ def theta_matrix(xv, xw, sign):
     return th
 
 
-def run_solve(tn, gram, chi, sign, n_edges):
+def run_solve(tn, gram, chi, sign, n_edges, solve="fp64"):
     import torch
     dev = torch.device("cuda")
     g = torch.from_numpy(gram.reshape(-1)).to(dev)
     d = torch.zeros_like(g)
     s = torch.zeros(n_edges * chi, dtype=torch.float64, device=dev)
     tn.truncation_solve(g.data_ptr(), d.data_ptr(), s.data_ptr(), n_edges, chi, sign,
-                        stream=torch.cuda.current_stream().cuda_stream)
+                        stream=torch.cuda.current_stream().cuda_stream, solve=solve)
     return d.cpu().numpy().reshape(gram.shape), s.cpu().numpy().reshape(n_edges, chi)
 
 
+@pytest.mark.parametrize("solve", ["fp64", "shared"])
 @pytest.mark.parametrize("sign", [1, -1])
-@pytest.mark.parametrize("chi,rows", [(4, 6), (8, 12), (16, 20)])
-def test_solve_matches_numpy_svd(tnlib, chi, rows, sign):
+@pytest.mark.parametrize("chi,rows", [(4, 6), (8, 12), (16, 20), (32, 40), (5, 3)])
+def test_solve_matches_numpy_svd(tnlib, chi, rows, sign, solve):
+    """Rows < chi makes the bond rank-deficient (padding regime)."""
     n_edges = 5
     xs, gram = make_case(chi, rows, n_edges, seed=chi + 7 * rows + (sign > 0))
-    dmat, s = run_solve(tnlib, gram, chi, sign, n_edges)
+    dmat, s = run_solve(tnlib, gram, chi, sign, n_edges, solve)
     for k in range(n_edges):
         xv, xw = xs[k]
         th = theta_matrix(xv, xw, sign)
         u, sv, vh = np.linalg.svd(th)
+        sv = np.where(sv > 1e-6 * sv[0], sv, 0.0)
         keep = sv[:chi] / np.linalg.norm(sv[:chi])
         assert np.allclose(s[k], keep, atol=2e-5 * keep[0])
         # rebuilt halves: left = X_v D_v, right = X_w D_w
