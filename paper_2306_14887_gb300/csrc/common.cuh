@@ -28,9 +28,11 @@ void set_error(const std::string& msg);
 //   C[m][n] (+)= alpha * sum_k opA(A)[m][k] * opB(B)[k][n]
 //
 // The contraction index k runs over K1 * K2 values, k = k1 * K2 + k2, so that
-// a contraction over two tensor legs with unrelated strides is one GEMM.
-// Element (m, k1, k2) of A is at A + m*a_m + k1*a_k1 + k2*a_k2; likewise B and
-// C.  Each operand is planar: the imaginary plane starts plane_* floats after
+// a contraction over two tensor legs with unrelated strides is one GEMM.  The
+// row index may likewise be two-level: with M2 > 1, m = m1 * M2 + m2 and row m
+// of A (C) starts at m1*a_m + m2*a_m2 (m1*c_m + m2*c_m2); with M2 <= 1 it
+// starts at m*a_m (m*c_m).  Element (m, k1, k2) of A is then at
+// A + row(m) + k1*a_k1 + k2*a_k2; likewise B (n*b_n + ...) and C.  Each operand is planar: the imaginary plane starts plane_* floats after
 // the real plane.  The batch is outer x inner: the outer index selects base
 // pointers from device arrays, the inner index adds inner * *_in.
 // ---------------------------------------------------------------------------
@@ -48,11 +50,24 @@ struct GemmDesc {
   int32_t conj_a, conj_b;
   int32_t accumulate;
   int32_t prec;  // tn_precision of the contraction
+  int32_t M2;
+  int64_t a_m2, c_m2;
 };
+
+__host__ __device__ __forceinline__ int64_t row_off(int m, int M2, int64_t s1, int64_t s2) {
+  if (M2 <= 1) return (int64_t)m * s1;
+  const int m1 = m / M2;
+  return (int64_t)m1 * s1 + (int64_t)(m - m1 * M2) * s2;
+}
 
 // Launch helpers implemented in kernels.cu / solve.cu.  All return a
 // cudaError_t from the launch.
 cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s);
+// Tensor-core version (tc_gemm.cu) for TN_TF32 / TN_BF16 descriptors.  part:
+// scratch for K-split partial products (tc_plan gives the size); err: bit 1 is
+// set when a device-side wait gave up.
+bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats);
+cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t s);
 
 // RX-type 2x2 on the physical leg: T[p] <- sum_q U[p][q] T[q] for every site in
 // the list.  site_off: float offset of each site's real plane; len: chi^d

@@ -86,6 +86,7 @@ struct tn_handle {
   int64_t t_floats = 0;
   float *T = nullptr, *Ts = nullptr, *Y1 = nullptr, *Y2 = nullptr;
   float *msg = nullptr, *raw = nullptr, *gram = nullptr, *dmat = nullptr;
+  float* part = nullptr;          // K-split partials of tensor-core closes
   double* work = nullptr;
   double* solve_stats = nullptr;
   int32_t* msg_vw = nullptr;      // per layer slot: directed ids of v->w and w->v
@@ -161,40 +162,34 @@ GemmDesc blank_desc(int prec) {
   d.n_inner = 1;
   d.K1 = 1;
   d.prec = prec;
+  d.M2 = 1;
   return d;
 }
 
 // Y = X x_j M on degree-d tensors (leg j contracted with M's row index, the
-// result keeps M's column index in place of leg j).  entries: (X, M, Y).
+// result keeps M's column index in place of leg j).  Rows are the other
+// indices (o, i): o = (p, legs before j), i = legs after j, a two-level row
+// index, so that every launch has 2 chi^(d-1) rows per site and the small
+// chi x chi matrix is the B operand.  entries: (X, M, Y).
 void add_mode_product(Plan& P, int d, int j, int chi, int prec,
-                      const std::vector<std::array<const float*, 3>>& ent) {
+                      const std::vector<std::array<const float*, 3>>& ent, bool with_p = true) {
   if (ent.empty()) return;
   HostLaunch L;
   L.d = blank_desc(prec);
   const int64_t inner = ipow(chi, d - 1 - j);
+  const int64_t outer = (with_p ? 2 : 1) * ipow(chi, j);
   const int64_t plane = 2 * ipow(chi, d);
   const int64_t c2 = (int64_t)chi * chi;
-  if (inner == 1) {  // rows (p, legs before j): Y = X M
-    L.d.M = (int)(2 * ipow(chi, d - 1));
-    L.d.N = chi;
-    L.d.K2 = chi;
-    L.d.a_m = chi; L.d.a_k2 = 1;
-    L.d.b_k2 = chi; L.d.b_n = 1;
-    L.d.c_m = chi; L.d.c_n = 1;
-    L.d.plane_a = plane; L.d.plane_b = c2; L.d.plane_c = plane;
-    for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
-  } else {           // per (p, legs before j): Y[o] = M^T X[o]
-    L.d.M = chi;
-    L.d.N = (int)inner;
-    L.d.K2 = chi;
-    L.d.a_m = 1; L.d.a_k2 = chi;
-    L.d.b_k2 = inner; L.d.b_n = 1;
-    L.d.c_m = inner; L.d.c_n = 1;
-    L.d.n_inner = (int)(2 * ipow(chi, j));
-    L.d.a_in = 0; L.d.b_in = chi * inner; L.d.c_in = chi * inner;
-    L.d.plane_a = c2; L.d.plane_b = plane; L.d.plane_c = plane;
-    for (auto& e : ent) { L.A.push_back(e[1]); L.B.push_back(e[0]); L.C.push_back((float*)e[2]); }
-  }
+  L.d.M = (int)(outer * inner);
+  L.d.N = chi;
+  L.d.K2 = chi;
+  L.d.M2 = (int)inner;
+  L.d.a_m = chi * inner; L.d.a_m2 = 1; L.d.a_k2 = inner;
+  L.d.b_k2 = chi; L.d.b_n = 1;
+  L.d.c_m = chi * inner; L.d.c_m2 = 1; L.d.c_n = inner;
+  if (inner == 1) { L.d.M2 = 1; L.d.a_m = chi; L.d.c_m = chi; }
+  L.d.plane_a = plane; L.d.plane_b = c2; L.d.plane_c = plane;
+  for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
   L.d.n_outer = (int)ent.size();
   P.L.push_back(std::move(L));
 }
@@ -230,38 +225,10 @@ void add_close(Plan& P, int d, int j, int chi, bool open_p, int prec,
 }
 
 // T'[p][.., n, ..] = sum_e T[p][.., e, ..] D_p[e][n] on leg j.  entries: (T_p, D_p, T'_p)
-// with one entry per (site, p).
+// with one entry per (site, p): the mode product without the p index.
 void add_leg_matrix(Plan& P, int d, int j, int chi, int prec,
                     const std::vector<std::array<const float*, 3>>& ent) {
-  if (ent.empty()) return;
-  HostLaunch L;
-  L.d = blank_desc(prec);
-  const int64_t inner = ipow(chi, d - 1 - j);
-  const int64_t plane = 2 * ipow(chi, d);
-  const int64_t c2 = (int64_t)chi * chi;
-  if (inner == 1) {
-    L.d.M = (int)ipow(chi, d - 1);
-    L.d.N = chi;
-    L.d.K2 = chi;
-    L.d.a_m = chi; L.d.a_k2 = 1;
-    L.d.b_k2 = chi; L.d.b_n = 1;
-    L.d.c_m = chi; L.d.c_n = 1;
-    L.d.plane_a = plane; L.d.plane_b = c2; L.d.plane_c = plane;
-    for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
-  } else {
-    L.d.M = chi;
-    L.d.N = (int)inner;
-    L.d.K2 = chi;
-    L.d.a_m = 1; L.d.a_k2 = chi;
-    L.d.b_k2 = inner; L.d.b_n = 1;
-    L.d.c_m = inner; L.d.c_n = 1;
-    L.d.n_inner = (int)ipow(chi, j);
-    L.d.a_in = 0; L.d.b_in = chi * inner; L.d.c_in = chi * inner;
-    L.d.plane_a = c2; L.d.plane_b = plane; L.d.plane_c = plane;
-    for (auto& e : ent) { L.A.push_back(e[1]); L.B.push_back(e[0]); L.C.push_back((float*)e[2]); }
-  }
-  L.d.n_outer = (int)ent.size();
-  P.L.push_back(std::move(L));
+  add_mode_product(P, d, j, chi, prec, ent, false);
 }
 
 tn_status upload_plans(tn_handle* h) {
@@ -383,10 +350,18 @@ void gemm_work(const GemmDesc& d, double* flops, double* bytes) {
   *bytes = 8.0 * (a + b + c);
 }
 
+bool use_tensor_cores(const tn_handle* h) {
+  return h->cfg.prec == TN_TF32 || h->cfg.prec == TN_BF16;
+}
+
 tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
   for (auto& L : P.L) {
     const int pi = prof_begin(h, cls);
-    TN_CUDA_TRY(launch_cgemm(L.d, h->stream));
+    if (use_tensor_cores(h)) {
+      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, h->stream));
+    } else {
+      TN_CUDA_TRY(launch_cgemm(L.d, h->stream));
+    }
     if (pi >= 0) {
       double f, b;
       gemm_work(L.d, &f, &b);
@@ -615,6 +590,10 @@ tn_status check_flags(tn_handle* h, const char* where) {
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (f) {
     TN_CUDA_TRY(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    if (f & 2) {
+      set_error(std::string("a device-side wait gave up in ") + where);
+      return TN_ETIMEOUT;
+    }
     set_error(std::string("non-finite or zero-norm values detected in ") + where);
     return TN_ENUMERIC;
   }
@@ -883,7 +862,10 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   *out = nullptr;
   if (cfg->chi < 1 || cfg->chi > 256) { set_error("chi must be in 1..256"); return TN_EINVAL; }
   if (cfg->prec < TN_FP32 || cfg->prec > TN_TF32X3) { set_error("unknown precision"); return TN_EINVAL; }
-  if (cfg->prec != TN_FP32) { set_error("precision mode not built yet"); return TN_EUNSUPPORTED; }
+  if (cfg->prec != TN_FP32 && cfg->prec != TN_TF32 && cfg->prec != TN_BF16) {
+    set_error("precision mode not built yet");
+    return TN_EUNSUPPORTED;
+  }
   if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64) {
     set_error("unknown truncation solve");
     return TN_EINVAL;
@@ -1001,6 +983,21 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->copyback.resize(nl);
   for (int li = 0; li < nl; ++li) build_gate_plans(h, li);
   build_rho_plan(h);
+  if (use_tensor_cores(h)) {
+    size_t need = 0;
+    std::vector<Plan*> plans = {&h->sweep, &h->rho_prep};
+    for (auto& p : h->gate_env) plans.push_back(&p);
+    for (auto& p : h->rebuild) plans.push_back(&p);
+    for (Plan* p : plans)
+      for (auto& L : p->L) {
+        int q, sp;
+        size_t pf = 0;
+        tc_plan(L.d, &q, &sp, &pf);
+        need = std::max(need, pf);
+      }
+    h->part = (float*)dev_alloc(h, sizeof(float) * std::max<size_t>(need, 16));
+    if (!h->part) { delete[] h->h_stats; set_error("device allocation failed"); return fail(TN_ENOMEM); }
+  }
   tn_status st = upload_plans(h);
   if (st) { delete[] h->h_stats; return fail(st); }
   st = init_state(h);

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int K = d.K1 * d.K2;
-  const bool a_kfast = (d.a_k2 == 1);
+  const bool a_kfast = (d.a_k2 == 1) && !(d.M2 > 1 && d.a_m2 == 1);
   const bool b_nfast = (d.b_n == 1);
   const float sa = d.conj_a ? -1.f : 1.f;
   const float sb = d.conj_b ? -1.f : 1.f;
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
       const int m = m0 + mm, k = k0 + kk;
       float re = 0.f, im = 0.f;
       if (m < d.M && k < K) {
-        const int64_t off = (int64_t)m * d.a_m + koff(k, d.K2, d.a_k1, d.a_k2);
+        const int64_t off = row_off(m, d.M2, d.a_m, d.a_m2) + koff(k, d.K2, d.a_k1, d.a_k2);
         re = A[off];
         im = sa * A[off + d.plane_a];
       }
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= d.N) continue;
-      const int64_t off = (int64_t)m * d.c_m + (int64_t)n * d.c_n;
+      const int64_t off = row_off(m, d.M2, d.c_m, d.c_m2) + (int64_t)n * d.c_n;
       if (d.accumulate) {
         C[off] += accr[i][j];
         C[off + d.plane_c] += acci[i][j];

@@ -1,0 +1,85 @@
+"""Tensor-core (tcgen05) contraction paths against the FP64 oracle.
+
+Stated bounds (mixed precision; FP32 accumulation, FP64 solve/normalisation):
+* one BP sweep from a random state, |dM| on unit-norm messages:
+  TF32 <= 1e-3, BF16 <= 5e-3 (operand rounding 2^-11 and 2^-9 relative);
+* full evolution, |d<Z>|: TF32 <= 5e-3, BF16 <= 5e-2 (the BP fixed point is
+  reached to the residual floor of the arithmetic, 2e-3 and 2e-2).
+"""
+import numpy as np
+import pytest
+
+from oracle import bptn as OB
+from oracle import graph as OG
+from workloads import random_state
+
+pytestmark = pytest.mark.gpu
+
+SWEEP_TOL = {"tf32": 1e-3, "bf16": 5e-3}
+Z_TOL = {"tf32": 5e-3, "bf16": 5e-2}
+
+
+@pytest.fixture(scope="module")
+def tnlib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_14887_gb300 import build
+    build.build()
+    import paper_2306_14887_gb300 as tn
+    return tn
+
+
+GRAPHS = {"star7": OG.star3_tree(), "ring12": OG.ring(12), "patch27": OG.falcon27_patch()}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("chi", [4, 8, 16, 32])
+def test_tensor_core_sweep_matches_oracle(tnlib, prec, name, chi):
+    g = GRAPHS[name]
+    tensors, msgs = random_state([g.degree(v) for v in range(g.n)], g.edges, chi, seed=11)
+    s = tnlib.TNState(g.n, g.edges, g.colours, chi=chi, prec=prec)
+    for v in range(g.n):
+        s.set_site(v, tensors[v])
+    for (src, e), m in msgs.items():
+        s.set_message(e, src, m)
+    it, res, _ = s.bp_converge(tol=1e30, max_iters=1)
+    o = OB.BPState(g, chi)
+    o.T = [t.astype(complex) for t in tensors]
+    o.M = {k: m.astype(complex) for k, m in msgs.items()}
+    o.bp_sweep()
+    err = max(np.abs(s.get_message(e, src) - o.M[(src, e)]).max() for (src, e) in o.M)
+    assert err < SWEEP_TOL[prec]
+    s.close()
+
+
+def test_tensor_core_sweep_chi64_degree3(tnlib):
+    g = GRAPHS["star7"]
+    chi = 64
+    tensors, msgs = random_state([g.degree(v) for v in range(g.n)], g.edges, chi, seed=3)
+    s = tnlib.TNState(g.n, g.edges, g.colours, chi=chi, prec="tf32")
+    for v in range(g.n):
+        s.set_site(v, tensors[v])
+    for (src, e), m in msgs.items():
+        s.set_message(e, src, m)
+    s.bp_converge(tol=1e30, max_iters=1)
+    o = OB.BPState(g, chi)
+    o.T = [t.astype(complex) for t in tensors]
+    o.M = {k: m.astype(complex) for k, m in msgs.items()}
+    o.bp_sweep()
+    err = max(np.abs(s.get_message(e, src) - o.M[(src, e)]).max() for (src, e) in o.M)
+    assert err < SWEEP_TOL["tf32"]
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("graph,chi,steps,theta", [
+    (OG.ring(12), 8, 5, 0.8), (OG.eagle127(), 16, 4, 0.6), (OG.eagle127(), 8, 6, 0.6)],
+    ids=["ring12", "eagle127-exact", "eagle127-truncated"])
+def test_tensor_core_evolution_within_stated_bound(tnlib, prec, graph, chi, steps, theta):
+    o = OB.run(graph, chi, theta, steps)
+    s = tnlib.TNState(graph.n, graph.edges, graph.colours, chi=chi, prec=prec)
+    s.apply_floquet(theta, steps)
+    assert np.abs(s.expect_z_all() - o.all_z()).max() < Z_TOL[prec]
+    s.close()
