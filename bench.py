@@ -58,7 +58,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--chi", type=int, default=64)
-    p.add_argument("--prec", default="fp32")
+    p.add_argument("--prec", default="tf32")
+    p.add_argument("--fp32-steps", type=int, default=3,
+                   help="timed steps of the plain FP32 path measured beside the main line (0: skip)")
     p.add_argument("--solve", default="auto", choices=["auto", "shared", "fp64"])
     p.add_argument("--theta", type=float, default=None)
     p.add_argument("--presteps", type=int, default=None)
@@ -164,12 +166,23 @@ def traffic_for(cls):
     return ent.get("dram_bytes_per_launch")
 
 
-def roofline(prof, prec):
+def bp_sweep_flops(chi, n_by_deg):
+    """Algorithmic real flops of one BP sweep: 16 chi^4 complex multiply-adds per
+    degree-3 site, 8 chi^3 per degree-2 site, 2 chi^2 per degree-1 site, 8 real
+    flops per complex multiply-add."""
+    return 8.0 * (16 * chi ** 4 * n_by_deg[3] + 8 * chi ** 3 * n_by_deg[2] + 2 * chi ** 2 * n_by_deg[1])
+
+
+def roofline(prof, prec, chi, sweeps, n_by_deg):
     cls = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[cls]
     n = max(1, p["launches"])
     ms_per = p["ms"] / n
     pk = peaks()
+    if cls == "bp_contract":
+        # algorithmic work of the sweeps, not the executed (padded, re-ordered) work
+        p = dict(p)
+        p["flops"] = bp_sweep_flops(chi, n_by_deg) * sweeps
     if cls == "trunc_solve":
         bound, unit, peak = "alu", "TFLOP/s", FP64_TFLOPS
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
@@ -178,10 +191,14 @@ def roofline(prof, prec):
         if prec == "fp32":
             bound, unit, peak = "alu", "TFLOP/s", FP32_SIMT_TFLOPS
             note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        elif prec == "bf16":
+            bound, unit = "tensor", "TFLOP/s"
+            peak = pk.get("bf16_tflops_sustained", 1715.0)
+            note = "bf16 sustained"
         else:
             bound, unit = "tensor", "TFLOP/s"
-            peak = pk.get("bf16_tflops", 1900.0) * TF32_OVER_BF16
-            note = "tf32 = measured bf16 burst x nominal tf32/bf16 ratio"
+            peak = pk.get("bf16_tflops_sustained", 1715.0) * TF32_OVER_BF16
+            note = "tf32 = measured bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)"
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
     else:
         bound, unit, peak = "hbm", "GB/s", pk.get("hbm_gbs", 6792.1)
@@ -306,14 +323,34 @@ def run_ours(args, rank, world, local):
                "d2h_bytes_per_step": 8 * n,
                "note": "fresh job per run: tn_create from the host graph, then per step "
                        "tn_apply_floquet + tn_expect_z_all (theta passed by value)"}
-    total_ms = sum(v["ms"] for v in prof.values())
-    rl = roofline(prof, args.prec)
+    nbd = {d: int(sum(1 for v in range(n) if int(np.sum(edges == v)) == d)) for d in (1, 2, 3)}
+    rl = roofline(prof, args.prec, chi, bp_iters, nbd)
     rl["share_of_timed"] = round(prof[rl["kernel"]]["ms"] / ms, 4)
+    fp32_line = None
+    if args.fp32_steps > 0 and args.prec != "fp32":
+        s3 = tn.TNState(n, edges, cols, chi=chi, prec="fp32", stream=stream)
+        s3.apply_floquet(theta, presteps + 1)
+        stream.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp32_steps):
+            s3.apply_floquet(theta, 1)
+        f1.record(stream)
+        stream.synchronize()
+        fms = f0.elapsed_time(f1)
+        zf = s3.expect_z_all()
+        s3.close()
+        fp32_line = {"value": round(args.fp32_steps / (fms * 1e-3), 4), "unit": UNIT,
+                     "steps": args.fp32_steps, "ms_per_step": round(fms / args.fp32_steps, 3),
+                     "note": "plain FP32 path (CUDA-core contractions, FP64 truncation solve), "
+                             "same workload and theta",
+                     "mixed_over_fp32": None}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32"}.get(args.prec, args.prec) + "+f64solve",
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}.get(args.prec, args.prec),
         "data": "synthetic (initial state |0..0>, theta_h from the uniform [0, pi/2] grid)",
         "config": {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, solve={args.solve}, "
                                f"theta_h={theta:.4f}, saturated after {presteps} steps",
@@ -329,7 +366,10 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "e2e": e2e,
         "z_mean": float(np.mean(z)),
+        "fp32_path": fp32_line,
     }
+    if fp32_line:
+        fp32_line["mixed_over_fp32"] = round(value / world / fp32_line["value"], 3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sec, det = oracle_step_estimate(chi, bp_iters / args.steps)
         out["cpu_baseline"] = {"value": round(1.0 / sec, 6), "unit": UNIT, "cores": blas_threads(),

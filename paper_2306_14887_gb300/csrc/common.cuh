@@ -50,15 +50,31 @@ struct GemmDesc {
   int32_t conj_a, conj_b;
   int32_t accumulate;
   int32_t prec;  // tn_precision of the contraction
-  int32_t M2;
-  int64_t a_m2, c_m2;
+  int32_t M2, M3;
+  int64_t a_m2, c_m2, a_m3, c_m3;
+  // b_pre: B points to the realified, transposed small operand, a real
+  // [2N][2K] row-major matrix Bt[(t,n)][(s,k)] = [[B_re, B_im], [-B_im, B_re]][s][t]
+  // (the fields b_n, b_k2, plane_b then describe its complex view).
+  int32_t b_pre;
 };
 
-__host__ __device__ __forceinline__ int64_t row_off(int m, int M2, int64_t s1, int64_t s2) {
+// Row offset for the two- or three-level row index: with M3 > 1,
+// m = (m1 * M2 + m2) * M3 + m3 and the offset is m1*s1 + m2*s2 + m3*s3; with
+// M3 <= 1 and M2 > 1, m = m1 * M2 + m2; otherwise m*s1.
+__host__ __device__ __forceinline__ int64_t row_off3(int m, int M2, int M3, int64_t s1,
+                                                     int64_t s2, int64_t s3) {
+  if (M3 > 1) {
+    const int m12 = m / M3;
+    const int m3 = m - m12 * M3;
+    const int m1 = m12 / M2;
+    return (int64_t)m1 * s1 + (int64_t)(m12 - m1 * M2) * s2 + (int64_t)m3 * s3;
+  }
   if (M2 <= 1) return (int64_t)m * s1;
   const int m1 = m / M2;
   return (int64_t)m1 * s1 + (int64_t)(m - m1 * M2) * s2;
 }
+#define ROW_A(d, m) row_off3((m), (d).M2, (d).M3, (d).a_m, (d).a_m2, (d).a_m3)
+#define ROW_C(d, m) row_off3((m), (d).M2, (d).M3, (d).c_m, (d).c_m2, (d).c_m3)
 
 // Launch helpers implemented in kernels.cu / solve.cu.  All return a
 // cudaError_t from the launch.
@@ -81,7 +97,18 @@ cudaError_t launch_phys_gate(float* T, const int64_t* site_off, int n_sites, int
 // res_bits: one unsigned long long holding the max residual as IEEE bits;
 // flags: bit 0 set on a non-finite or zero-norm message.
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
-                             unsigned long long* res_bits, int* flags, cudaStream_t s);
+                             unsigned long long* res_bits, int* flags, cudaStream_t s,
+                             float* mrt = nullptr);
+
+// Realified transposed copies of n planar complex chi x chi matrices (each at
+// src + i*src_stride): dst + i*4chi^2 holds Bt[(t,n)][(s,k)] as in GemmDesc::b_pre.
+cudaError_t launch_realify(const float* src, int64_t src_stride, float* dst, int n, int chi,
+                           cudaStream_t s);
+
+// TA copies of site tensors with the first leg moved last:
+// TA[pl][p][l1..l_{d-1}][l0] = T[pl][p][l0][l1..l_{d-1}] (planar).
+cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site_off, int n_sites,
+                                  int d, int chi, cudaStream_t s);
 
 // rho[site][p][p'] = sum_r X[p][r] conj(T[p'][r]) in FP64 (complex, 8 doubles
 // per site).  x_off / t_off: real-plane offsets; len = chi^d; plane = 2*len.

@@ -87,6 +87,10 @@ struct tn_handle {
   float *T = nullptr, *Ts = nullptr, *Y1 = nullptr, *Y2 = nullptr;
   float *msg = nullptr, *raw = nullptr, *gram = nullptr, *dmat = nullptr;
   float* part = nullptr;          // K-split partials of tensor-core closes
+  float* TA = nullptr;            // site tensors with the first leg moved last
+  float* mrt = nullptr;           // realified transposed messages [2E][2chi][2chi]
+  float* drt = nullptr;           // realified transposed leg matrices [slot][side][p][2chi][2chi]
+  bool ta_valid = false, mrt_valid = false;
   double* work = nullptr;
   double* solve_stats = nullptr;
   int32_t* msg_vw = nullptr;      // per layer slot: directed ids of v->w and w->v
@@ -222,13 +226,6 @@ void add_close(Plan& P, int d, int j, int chi, bool open_p, int prec,
   for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
   L.d.n_outer = (int)ent.size();
   P.L.push_back(std::move(L));
-}
-
-// T'[p][.., n, ..] = sum_e T[p][.., e, ..] D_p[e][n] on leg j.  entries: (T_p, D_p, T'_p)
-// with one entry per (site, p): the mode product without the p index.
-void add_leg_matrix(Plan& P, int d, int j, int chi, int prec,
-                    const std::vector<std::array<const float*, 3>>& ent) {
-  add_mode_product(P, d, j, chi, prec, ent, false);
 }
 
 tn_status upload_plans(tn_handle* h) {
@@ -383,78 +380,191 @@ const float* in_msg(const tn_handle* h, int v, int e) {
 
 using Ent = std::array<const float*, 3>;
 
-void build_sweep_plan(tn_handle* h) {
-  const int chi = h->chi, prec = h->cfg.prec;
-  Plan& P = h->sweep;
+// A contraction spec: every stride of a GemmDesc, filled by the builders below.
+struct Spec {
+  int M, N, K1 = 1, K2, M2 = 1, M3 = 1;
+  int64_t a_m, a_m2 = 0, a_m3 = 0, a_k1 = 0, a_k2;
+  int64_t b_n, b_k1 = 0, b_k2;
+  int64_t c_m, c_m2 = 0, c_m3 = 0, c_n;
+  int64_t plane_a, plane_b, plane_c;
+  int n_inner = 1;
+  int64_t a_in = 0, b_in = 0, c_in = 0;
+  int conj_b = 0, b_pre = 0;
+};
+
+void add_spec(Plan& P, const Spec& sp, int prec, const std::vector<Ent>& ent) {
+  if (ent.empty()) return;
+  HostLaunch L;
+  L.d = blank_desc(prec);
+  GemmDesc& d = L.d;
+  d.M = sp.M; d.N = sp.N; d.K1 = sp.K1; d.K2 = sp.K2; d.M2 = sp.M2; d.M3 = sp.M3;
+  d.a_m = sp.a_m; d.a_m2 = sp.a_m2; d.a_m3 = sp.a_m3; d.a_k1 = sp.a_k1; d.a_k2 = sp.a_k2;
+  d.b_n = sp.b_n; d.b_k1 = sp.b_k1; d.b_k2 = sp.b_k2;
+  d.c_m = sp.c_m; d.c_m2 = sp.c_m2; d.c_m3 = sp.c_m3; d.c_n = sp.c_n;
+  d.plane_a = sp.plane_a; d.plane_b = sp.plane_b; d.plane_c = sp.plane_c;
+  d.n_inner = sp.n_inner; d.a_in = sp.a_in; d.b_in = sp.b_in; d.c_in = sp.c_in;
+  d.conj_b = sp.conj_b; d.b_pre = sp.b_pre;
+  for (auto& e : ent) { L.A.push_back(e[0]); L.B.push_back(e[1]); L.C.push_back((float*)e[2]); }
+  d.n_outer = (int)ent.size();
+  P.L.push_back(std::move(L));
+}
+
+// Mode product Y = X x_leg Mt with the contracted leg fastest in X's rows (each
+// row of X holds chi contiguous values of the contracted leg) and the small
+// operand given realified and transposed (b_pre).  rows: number of rows per
+// entry; the row levels and output strides come from the caller.
+Spec mode_spec(int chi, int64_t plane, int M, int M2, int M3, int64_t a_m, int64_t a_m2,
+               int64_t a_m3, int64_t c_m, int64_t c_m2, int64_t c_m3, int64_t c_n) {
+  Spec sp;
+  sp.M = M; sp.N = chi; sp.K1 = 1; sp.K2 = chi; sp.M2 = M2; sp.M3 = M3;
+  sp.a_m = a_m; sp.a_m2 = a_m2; sp.a_m3 = a_m3; sp.a_k2 = 1;
+  sp.b_pre = 1; sp.b_n = 2 * chi; sp.b_k1 = chi; sp.b_k2 = 1; sp.plane_b = 2LL * chi * chi;
+  sp.c_m = c_m; sp.c_m2 = c_m2; sp.c_m3 = c_m3; sp.c_n = c_n;
+  sp.plane_a = plane; sp.plane_c = plane;
+  return sp;
+}
+
+// Close out[e][e'] = sum_K Y[e][K] conj(X[e'][K]) with both operands K-contiguous.
+Spec close_spec(int chi, int64_t plane, int K1, int K2, int64_t a_m, int64_t a_k1, int64_t b_n,
+                int64_t b_k1) {
+  Spec sp;
+  sp.M = chi; sp.N = chi; sp.K1 = K1; sp.K2 = K2;
+  sp.a_m = a_m; sp.a_k1 = a_k1; sp.a_k2 = 1;
+  sp.b_n = b_n; sp.b_k1 = b_k1; sp.b_k2 = 1;
+  sp.c_m = chi; sp.c_n = 1;
+  sp.plane_a = plane; sp.plane_b = plane; sp.plane_c = (int64_t)chi * chi;
+  sp.conj_b = 1;
+  return sp;
+}
+
+const float* mrt_ptr(const tn_handle* h, int did) {
+  return h->mrt + (int64_t)did * 4 * h->chi * h->chi;
+}
+// realified transposed incoming message into v along edge e
+const float* in_mrt(const tn_handle* h, int v, int e) {
+  return mrt_ptr(h, dir_id(h->g, h->g.other(e, v), e));
+}
+
+// Degree-3 chains (legs a, b, c of T[p][a][b][c]; TA[p][b][c][a]):
+//   A1  Y1[(p,a,c')][b]   = T  x_c Mc        A2  Y2[a][p][b'][c'] = Y1 x_b Mb
+//   B1  Y1[(p,b,c')][a]   = T  x_c Mc        B2  Y2[b][p][a'][c'] = Y1 x_a Ma
+//   C1  Y1[(p,c,a')][b]   = TA x_a Ma        C2  Y2[c][p][b'][a'] = Y1 x_b Mb
+// each followed by the close on the open leg against T (chains A, B) or TA (C).
+void deg3_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites, bool open_p,
+                const std::vector<float*>& outs) {
+  const int x = h->chi, prec = h->cfg.prec;
+  const int64_t x2 = (int64_t)x * x, x3 = x2 * x, plane = 2 * x3;
   const HostGraph& g = h->g;
-  // degree 3: Yc, Ybc -> out_0; Yac -> out_1; Ya, Yab -> out_2
-  std::vector<Ent> m1, m2, c0, m3, c1, m4, m5, c2;
-  for (int v : h->sites_by_deg[3]) {
+  std::vector<Ent> e1, e2, ec;
+  for (size_t i = 0; i < sites.size(); ++i) {
+    const int v = sites[i];
     const auto& lg = g.legs[v];
     const float* T = site_ptr(h, h->T, v);
+    const float* TA = site_ptr(h, h->TA, v);
     const float* Y1 = site_ptr(h, h->Y1, v);
     const float* Y2 = site_ptr(h, h->Y2, v);
-    m1.push_back({T, in_msg(h, v, lg[2]), Y1});
-    m2.push_back({Y1, in_msg(h, v, lg[1]), Y2});
-    c0.push_back({Y2, T, msg_ptr(h, h->raw, dir_id(g, v, lg[0]))});
+    if (which == 0) {
+      e1.push_back({T, in_mrt(h, v, lg[2]), Y1});
+      e2.push_back({Y1, in_mrt(h, v, lg[1]), Y2});
+      ec.push_back({Y2, T, outs[i]});
+    } else if (which == 1) {
+      e1.push_back({T, in_mrt(h, v, lg[2]), Y1});
+      e2.push_back({Y1, in_mrt(h, v, lg[0]), Y2});
+      ec.push_back({Y2, T, outs[i]});
+    } else {
+      e1.push_back({TA, in_mrt(h, v, lg[0]), Y1});
+      e2.push_back({Y1, in_mrt(h, v, lg[1]), Y2});
+      ec.push_back({Y2, TA, outs[i]});
+    }
   }
-  add_mode_product(P, 3, 2, chi, prec, m1);
-  add_mode_product(P, 3, 1, chi, prec, m2);
-  add_close(P, 3, 0, chi, false, prec, c0);
-  for (int v : h->sites_by_deg[3]) {
+  const int M = (int)(2 * x2);
+  Spec s1, s2, sc;
+  if (which == 0) {
+    // rows (p,a,b) of T -> Y1 at (pa) x^2 + c' x + b
+    s1 = mode_spec(x, plane, M, x, 1, x2, x, 0, x2, 1, 0, x);
+    // rows (p,a,c') of Y1 -> Y2 at a 2x^2 + p x^2 + b' x + c'
+    s2 = mode_spec(x, plane, M, x, x, x3, x2, x, x2, 2 * x2, 1, x);
+    sc = close_spec(x, plane, 2, (int)x2, 2 * x2, x2, x2, x3);
+    if (open_p) { sc.K1 = 1; sc.n_inner = 2; sc.a_in = x2; sc.b_in = x3; sc.c_in = 2 * x2; }
+  } else if (which == 1) {
+    // rows enumerated (p,b,a) so that a, contiguous in the output, is the fastest
+    // row index: T row at p x^3 + a x^2 + b x -> Y1 at p x^3 + b x^2 + c' x + a
+    s1 = mode_spec(x, plane, M, x, x, x3, x, x2, x3, x2, 1, x);
+    // rows (p,b,c') of Y1 -> Y2 at b 2x^2 + p x^2 + a' x + c'
+    s2 = mode_spec(x, plane, M, x, x, x3, x2, x, x2, 2 * x2, 1, x);
+    sc = close_spec(x, plane, 2 * x, x, 2 * x2, x, x, x2);
+    if (open_p) { sc.K1 = x; sc.n_inner = 2; sc.a_in = x2; sc.b_in = x3; sc.c_in = 2 * x2; }
+  } else {
+    // rows enumerated (p,c,b): TA row at p x^3 + b x^2 + c x -> Y1 at
+    // p x^3 + c x^2 + a' x + b (b, the fastest row index, contiguous)
+    s1 = mode_spec(x, plane, M, x, x, x3, x, x2, x3, x2, 1, x);
+    // rows (p,c,a') of Y1 -> Y2 at c 2x^2 + p x^2 + b' x + a'
+    s2 = mode_spec(x, plane, M, x, x, x3, x2, x, x2, 2 * x2, 1, x);
+    sc = close_spec(x, plane, 2 * x, x, 2 * x2, x, x, x2);
+    if (open_p) { sc.K1 = x; sc.n_inner = 2; sc.a_in = x2; sc.b_in = x3; sc.c_in = 2 * x2; }
+  }
+  add_spec(P, s1, prec, e1);
+  add_spec(P, s2, prec, e2);
+  add_spec(P, sc, prec, ec);
+}
+
+// Degree-2 chains (T[p][a][b], TA[p][b][a]):
+//   which 0: Y1[a][p][b'] = T x_b Mb, close on a against T
+//   which 1: Y1[b][p][a'] = TA x_a Ma, close on b against TA
+void deg2_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites, bool open_p,
+                const std::vector<float*>& outs) {
+  const int x = h->chi, prec = h->cfg.prec;
+  const int64_t x2 = (int64_t)x * x, plane = 2 * x2;
+  const HostGraph& g = h->g;
+  std::vector<Ent> e1, ec;
+  for (size_t i = 0; i < sites.size(); ++i) {
+    const int v = sites[i];
     const auto& lg = g.legs[v];
-    const float* T = site_ptr(h, h->T, v);
-    const float* Y1 = site_ptr(h, h->Y1, v);
-    const float* Y2 = site_ptr(h, h->Y2, v);
-    m3.push_back({Y1, in_msg(h, v, lg[0]), Y2});
-    c1.push_back({Y2, T, msg_ptr(h, h->raw, dir_id(g, v, lg[1]))});
+    const float* src = site_ptr(h, which == 0 ? h->T : h->TA, v);
+    const float* Y1 = site_ptr(h, which == 0 ? h->Y1 : h->Y2, v);
+    e1.push_back({src, in_mrt(h, v, lg[which == 0 ? 1 : 0]), Y1});
+    ec.push_back({Y1, src, outs[i]});
   }
-  add_mode_product(P, 3, 0, chi, prec, m3);
-  add_close(P, 3, 1, chi, false, prec, c1);
-  for (int v : h->sites_by_deg[3]) {
-    const auto& lg = g.legs[v];
-    const float* T = site_ptr(h, h->T, v);
-    const float* Y1 = site_ptr(h, h->Y1, v);
-    const float* Y2 = site_ptr(h, h->Y2, v);
-    m4.push_back({T, in_msg(h, v, lg[0]), Y1});
-    m5.push_back({Y1, in_msg(h, v, lg[1]), Y2});
-    c2.push_back({Y2, T, msg_ptr(h, h->raw, dir_id(g, v, lg[2]))});
+  // rows (p, l) of the source -> Y1 at l 2x + p x + n
+  Spec s1 = mode_spec(x, plane, (int)(2 * x), x, 1, x2, x, 0, x, 2 * x, 0, 1);
+  Spec sc = close_spec(x, plane, 2, x, 2 * x, x, x, x2);
+  if (open_p) { sc.K1 = 1; sc.n_inner = 2; sc.a_in = x; sc.b_in = x2; sc.c_in = 2 * x2; }
+  add_spec(P, s1, prec, e1);
+  add_spec(P, sc, prec, ec);
+}
+
+void build_sweep_plan(tn_handle* h) {
+  const HostGraph& g = h->g;
+  Plan& P = h->sweep;
+  const std::vector<int>& s3 = h->sites_by_deg[3];
+  for (int which = 0; which < 3; ++which) {
+    std::vector<float*> outs;
+    for (int v : s3) outs.push_back((float*)msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][which])));
+    deg3_chain(h, P, which, s3, false, outs);
   }
-  add_mode_product(P, 3, 0, chi, prec, m4);
-  add_mode_product(P, 3, 1, chi, prec, m5);
-  add_close(P, 3, 2, chi, false, prec, c2);
-  // degree 2: Ya -> out_1 ; Yb -> out_0
-  std::vector<Ent> a1, ac1, a2, ac0;
-  for (int v : h->sites_by_deg[2]) {
-    const auto& lg = g.legs[v];
-    const float* T = site_ptr(h, h->T, v);
-    a1.push_back({T, in_msg(h, v, lg[0]), site_ptr(h, h->Y1, v)});
-    ac1.push_back({site_ptr(h, h->Y1, v), T, msg_ptr(h, h->raw, dir_id(g, v, lg[1]))});
-    a2.push_back({T, in_msg(h, v, lg[1]), site_ptr(h, h->Y2, v)});
-    ac0.push_back({site_ptr(h, h->Y2, v), T, msg_ptr(h, h->raw, dir_id(g, v, lg[0]))});
+  const std::vector<int>& s2 = h->sites_by_deg[2];
+  for (int which = 0; which < 2; ++which) {
+    std::vector<float*> outs;
+    for (int v : s2) outs.push_back((float*)msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][which])));
+    deg2_chain(h, P, which, s2, false, outs);
   }
-  add_mode_product(P, 2, 0, chi, prec, a1);
-  add_close(P, 2, 1, chi, false, prec, ac1);
-  add_mode_product(P, 2, 1, chi, prec, a2);
-  add_close(P, 2, 0, chi, false, prec, ac0);
-  // degree 1
   std::vector<Ent> d1;
   for (int v : h->sites_by_deg[1]) {
     const float* T = site_ptr(h, h->T, v);
     d1.push_back({T, T, msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][0]))});
   }
-  add_close(P, 1, 0, chi, false, prec, d1);
+  add_close(P, 1, 0, h->chi, false, h->cfg.prec, d1);
 }
 
-// Environments of both sides of every edge in layer `li`, open p, into gram.
+// Environments of both sides of every edge in layer `li`, open p, into gram;
+// rebuild of both site tensors from the solve's leg matrices, into Ts.
 void build_gate_plans(tn_handle* h, int li) {
-  const int chi = h->chi, prec = h->cfg.prec;
+  const int x = h->chi, prec = h->cfg.prec;
   const HostGraph& g = h->g;
   const auto& layer = g.layers[li];
-  const int64_t c2 = (int64_t)chi * chi;
+  const int64_t c2 = (int64_t)x * x;
   Plan env, reb;
-  // group sides by (degree, leg position)
-  std::vector<std::array<int, 3>> sides[4][3];  // (v, slot, side)
+  std::vector<std::array<int, 3>> sides[4][3];  // (v, slot, side) by (degree, leg position)
   for (int s = 0; s < (int)layer.size(); ++s) {
     const int e = layer[s];
     const int ends[2] = {g.eu[e], g.ew[e]};
@@ -464,74 +574,60 @@ void build_gate_plans(tn_handle* h, int li) {
     }
   }
   auto gram_ptr = [&](int slot, int side) { return h->gram + ((int64_t)slot * 2 + side) * 4 * c2; };
-  auto dmat_ptr = [&](int slot, int side, int p) {
-    return h->dmat + ((int64_t)slot * 2 + side) * 4 * c2 + p * 2 * c2;
+  auto drt_ptr = [&](int slot, int side, int p) {
+    return h->drt + (((int64_t)slot * 2 + side) * 2 + p) * 4 * c2;
   };
-  // degree 1
+  for (int j = 0; j < 3; ++j) {
+    std::vector<int> vs;
+    std::vector<float*> outs;
+    for (auto& sd : sides[3][j]) { vs.push_back(sd[0]); outs.push_back(gram_ptr(sd[1], sd[2])); }
+    if (!vs.empty()) deg3_chain(h, env, j, vs, true, outs);
+  }
+  for (int j = 0; j < 2; ++j) {
+    std::vector<int> vs;
+    std::vector<float*> outs;
+    for (auto& sd : sides[2][j]) { vs.push_back(sd[0]); outs.push_back(gram_ptr(sd[1], sd[2])); }
+    if (!vs.empty()) deg2_chain(h, env, j, vs, true, outs);
+  }
   {
     std::vector<Ent> c;
-    for (auto& s : sides[1][0]) {
-      const float* T = site_ptr(h, h->T, s[0]);
-      c.push_back({T, T, gram_ptr(s[1], s[2])});
+    for (auto& sd : sides[1][0]) {
+      const float* T = site_ptr(h, h->T, sd[0]);
+      c.push_back({T, T, gram_ptr(sd[1], sd[2])});
     }
-    add_close(env, 1, 0, chi, true, prec, c);
+    add_close(env, 1, 0, x, true, prec, c);
   }
-  // degree 2, gate on leg 1: Ya = T x_0 M0 ; gate on leg 0: Yb = T x_1 M1
-  {
-    std::vector<Ent> m, c;
-    for (auto& s : sides[2][1]) {
-      const int v = s[0];
-      const float* T = site_ptr(h, h->T, v);
-      m.push_back({T, in_msg(h, v, g.legs[v][0]), site_ptr(h, h->Y1, v)});
-      c.push_back({site_ptr(h, h->Y1, v), T, gram_ptr(s[1], s[2])});
-    }
-    add_mode_product(env, 2, 0, chi, prec, m);
-    add_close(env, 2, 1, chi, true, prec, c);
-    m.clear(); c.clear();
-    for (auto& s : sides[2][0]) {
-      const int v = s[0];
-      const float* T = site_ptr(h, h->T, v);
-      m.push_back({T, in_msg(h, v, g.legs[v][1]), site_ptr(h, h->Y1, v)});
-      c.push_back({site_ptr(h, h->Y1, v), T, gram_ptr(s[1], s[2])});
-    }
-    add_mode_product(env, 2, 1, chi, prec, m);
-    add_close(env, 2, 0, chi, true, prec, c);
-  }
-  // degree 3
-  for (int j = 0; j < 3; ++j) {
-    std::vector<Ent> m1, m2, c;
-    // contract the two legs other than j: first the higher one, then the lower
-    int o[2];
-    int k = 0;
-    for (int q = 2; q >= 0; --q)
-      if (q != j) o[k++] = q;
-    for (auto& s : sides[3][j]) {
-      const int v = s[0];
-      const float* T = site_ptr(h, h->T, v);
-      m1.push_back({T, in_msg(h, v, g.legs[v][o[0]]), site_ptr(h, h->Y1, v)});
-      m2.push_back({site_ptr(h, h->Y1, v), in_msg(h, v, g.legs[v][o[1]]), site_ptr(h, h->Y2, v)});
-      c.push_back({site_ptr(h, h->Y2, v), T, gram_ptr(s[1], s[2])});
-    }
-    add_mode_product(env, 3, o[0], chi, prec, m1);
-    add_mode_product(env, 3, o[1], chi, prec, m2);
-    add_close(env, 3, j, chi, true, prec, c);
-  }
-  // rebuild: T'_p = T_p x_leg D_p, into Ts; then copy back
+  // rebuild T'_p = T_p x_leg D_p for each (site, p), the contracted leg read
+  // where it is fastest (T for the last leg, TA for the first leg)
+  const int64_t x2 = c2;
   std::vector<CopyLaunch> cps(4);
   for (int d = 1; d <= 3; ++d)
     for (int j = 0; j < d; ++j) {
+      if (sides[d][j].empty()) continue;
+      const int64_t plane = 2 * ipow(x, d);
+      const bool first = (j == 0 && d >= 2);
       std::vector<Ent> ent;
-      for (auto& s : sides[d][j]) {
-        const int v = s[0];
+      for (auto& sd : sides[d][j]) {
+        const int v = sd[0];
         const int64_t len = h->t_len[v];
         for (int p = 0; p < 2; ++p)
-          ent.push_back({site_ptr(h, h->T, v) + p * len, dmat_ptr(s[1], s[2], p),
+          ent.push_back({site_ptr(h, first ? h->TA : h->T, v) + p * len, drt_ptr(sd[1], sd[2], p),
                          site_ptr(h, h->Ts, v) + p * len});
         cps[d].dst.push_back(h->T + h->t_off[v]);
         cps[d].src.push_back(h->Ts + h->t_off[v]);
         cps[d].n_floats = 4 * len;
       }
-      add_leg_matrix(reb, d, j, chi, prec, ent);
+      Spec sp;
+      if (d == 3 && j == 2) sp = mode_spec(x, plane, (int)x2, 1, 1, x, 0, 0, x, 0, 0, 1);
+      else if (d == 3 && j == 0) sp = mode_spec(x, plane, (int)x2, 1, 1, x, 0, 0, 1, 0, 0, x2);
+      else if (d == 3 && j == 1) {
+        // rows (a, c), the contracted leg b at stride chi
+        sp = mode_spec(x, plane, (int)x2, x, 1, x2, 1, 0, x2, 1, 0, x);
+        sp.a_k2 = x;
+      } else if (d == 2 && j == 1) sp = mode_spec(x, plane, x, 1, 1, x, 0, 0, x, 0, 0, 1);
+      else if (d == 2 && j == 0) sp = mode_spec(x, plane, x, 1, 1, x, 0, 0, 1, 0, 0, x);
+      else sp = mode_spec(x, plane, 1, 1, 1, x, 0, 0, x, 0, 0, 1);  // degree 1
+      add_spec(reb, sp, prec, ent);
     }
   h->gate_env[li] = std::move(env);
   h->rebuild[li] = std::move(reb);
@@ -600,7 +696,31 @@ tn_status check_flags(tn_handle* h, const char* where) {
   return TN_OK;
 }
 
+// TA (first leg last) must match T before any plan that reads it.
+tn_status ensure_ta(tn_handle* h) {
+  if (h->ta_valid) return TN_OK;
+  for (int d = 2; d <= 3; ++d) {
+    if (!h->n_by_deg[d]) continue;
+    TN_CUDA_TRY(launch_first_leg_last(h->T, h->TA, h->site_offs_by_deg[d], h->n_by_deg[d], d,
+                                      h->chi, h->stream));
+    h->stats.kernel_launches++;
+  }
+  h->ta_valid = true;
+  return TN_OK;
+}
+
+// The realified transposed messages must match msg before any mode product.
+tn_status ensure_mrt(tn_handle* h) {
+  if (h->mrt_valid) return TN_OK;
+  const int nmsg = 2 * (int)h->g.eu.size();
+  TN_CUDA_TRY(launch_realify(h->msg, 2LL * h->chi * h->chi, h->mrt, nmsg, h->chi, h->stream));
+  h->stats.kernel_launches++;
+  h->mrt_valid = true;
+  return TN_OK;
+}
+
 tn_status phys_gate(tn_handle* h, const double u[8]) {
+  h->ta_valid = false;
   for (int d = 1; d <= 3; ++d) {
     if (!h->n_by_deg[d]) continue;
     const int64_t len = ipow(h->chi, d);
@@ -644,7 +764,11 @@ double precision_floor(const tn_handle* h) {
 }
 
 tn_status gate_layer(tn_handle* h, int li, int sign) {
-  tn_status st = run_plan(h, h->gate_env[li], P_ENV);
+  tn_status st = ensure_ta(h);
+  if (st) return st;
+  st = ensure_mrt(h);
+  if (st) return st;
+  st = run_plan(h, h->gate_env[li], P_ENV);
   if (st) return st;
   SolveArgs a;
   a.n_edges = (int)h->g.layers[li].size();
@@ -673,8 +797,13 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
     prof_end(h, pi, 40.0 * n * n * n * a.n_edges, 4.0 * 16.0 * h->chi * h->chi * a.n_edges);
   }
   h->stats.kernel_launches++;
+  h->mrt_valid = false;  // the solve rewrote the gate-edge messages
+  TN_CUDA_TRY(launch_realify(h->dmat, 2LL * h->chi * h->chi, h->drt, 4 * a.n_edges, h->chi,
+                             h->stream));
+  h->stats.kernel_launches++;
   st = run_plan(h, h->rebuild[li], P_REBUILD);
   if (st) return st;
+  h->ta_valid = false;
   for (auto& c : h->copyback[li]) {
     const int pi = prof_begin(h, P_COPY);
     TN_CUDA_TRY(launch_copy_blocks(c.d_dst, c.d_src, (int)c.dst.size(), c.n_floats, h->stream));
@@ -707,12 +836,19 @@ tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, 
   std::vector<double> hist;
   bool stagnated = false;
   int it = 0;
+  {
+    tn_status st0 = ensure_ta(h);
+    if (st0) return st0;
+    st0 = ensure_mrt(h);
+    if (st0) return st0;
+  }
   for (it = 1; it <= max_iters; ++it) {
     TN_CUDA_TRY(cudaMemsetAsync(h->res_bits, 0, sizeof(unsigned long long), h->stream));
     tn_status st = run_plan(h, h->sweep, P_BP);
     if (st) return st;
     const int pi = prof_begin(h, P_NORM);
-    TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream));
+    TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream,
+                                 h->mrt));
     prof_end(h, pi, 0.0, 3.0 * 8.0 * h->chi * h->chi * nmsg);
     h->stats.kernel_launches++;
     unsigned long long bits = 0;
@@ -793,6 +929,8 @@ tn_status init_state(tn_handle* h) {
     TN_CUDA_TRY(cudaMemcpyAsync(h->msg + (int64_t)m * 2 * c2, &one, sizeof(float),
                                 cudaMemcpyHostToDevice, h->stream));
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->ta_valid = false;
+  h->mrt_valid = false;
   return TN_OK;
 }
 
@@ -803,7 +941,9 @@ size_t footprint_of(const HostGraph& g, int chi) {
   size_t maxl = 0;
   for (auto& l : g.layers) maxl = std::max(maxl, l.size());
   size_t b = 0;
-  b += 4 * sizeof(float) * (size_t)tf;                      // T, Ts, Y1, Y2
+  b += 5 * sizeof(float) * (size_t)tf;                      // T, Ts, TA, Y1, Y2
+  b += sizeof(float) * (size_t)(2 * g.eu.size()) * 4 * c2;  // realified messages
+  b += sizeof(float) * maxl * 16 * c2;                     // realified leg matrices
   b += 2 * sizeof(float) * (size_t)(2 * g.eu.size()) * 2 * c2;  // msg, raw
   b += 2 * sizeof(float) * maxl * 8 * c2;                  // gram, dmat
   b += sizeof(double) * maxl * solve_work_doubles(chi);    // work
@@ -924,10 +1064,13 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->Ts = (float*)dev_alloc(h, sizeof(float) * off);
   h->Y1 = (float*)dev_alloc(h, sizeof(float) * off);
   h->Y2 = (float*)dev_alloc(h, sizeof(float) * off);
+  h->TA = (float*)dev_alloc(h, sizeof(float) * off);
+  h->mrt = (float*)dev_alloc(h, sizeof(float) * nmsg * 4 * c2);
   h->msg = (float*)dev_alloc(h, sizeof(float) * nmsg * 2 * c2);
   h->raw = (float*)dev_alloc(h, sizeof(float) * nmsg * 2 * c2);
   h->gram = (float*)dev_alloc(h, sizeof(float) * h->max_layer * 8 * c2);
   h->dmat = (float*)dev_alloc(h, sizeof(float) * h->max_layer * 8 * c2);
+  h->drt = (float*)dev_alloc(h, sizeof(float) * h->max_layer * 16 * c2);
   h->work = (double*)dev_alloc(h, sizeof(double) * h->max_layer * solve_work_doubles(chi));
   h->solve_stats = (double*)dev_alloc(h, sizeof(double) * 4 * h->max_layer);
   h->res_bits = (unsigned long long*)dev_alloc(h, 64);
@@ -947,7 +1090,8 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
       return fail(TN_ENOMEM);
     }
   }
-  if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->msg || !h->raw || !h->gram || !h->dmat ||
+  if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->TA || !h->mrt || !h->drt || !h->msg ||
+      !h->raw || !h->gram || !h->dmat ||
       !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho) {
     set_error("device allocation failed (footprint " + std::to_string(footprint_of(g, chi)) +
               " bytes)");
@@ -1116,6 +1260,10 @@ static tn_status backup_state(tn_handle* h, bool restore) {
   TN_CUDA_TRY(cudaMemcpyAsync(dst_t, src_t, sizeof(float) * h->t_floats, cudaMemcpyDeviceToDevice,
                               h->stream));
   TN_CUDA_TRY(cudaMemcpyAsync(dst_m, src_m, mb, cudaMemcpyDeviceToDevice, h->stream));
+  if (restore) {
+    h->ta_valid = false;
+    h->mrt_valid = false;
+  }
   return TN_OK;
 }
 
@@ -1276,6 +1424,7 @@ static tn_status site_io(tn_handle* h, int v, float* buf, size_t n_floats, bool 
     TN_CUDA_TRY(cudaMemcpyAsync(h->T + h->t_off[v], planar.data(), sizeof(float) * 4 * len,
                                 cudaMemcpyHostToDevice, h->stream));
     TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->ta_valid = false;
   }
   return TN_OK;
 }
@@ -1307,6 +1456,7 @@ static tn_status msg_io(tn_handle* h, int e, int src, float* buf, size_t n_float
     TN_CUDA_TRY(cudaMemcpyAsync(dev, planar.data(), sizeof(float) * 2 * c2, cudaMemcpyHostToDevice,
                                 h->stream));
     TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->mrt_valid = false;
   }
   return TN_OK;
 }

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int K = d.K1 * d.K2;
-  const bool a_kfast = (d.a_k2 == 1) && !(d.M2 > 1 && d.a_m2 == 1);
+  const bool a_kfast = (d.a_k2 == 1) && !(d.M2 > 1 && d.M3 <= 1 && d.a_m2 == 1) &&
+                       !(d.M3 > 1 && d.a_m3 == 1);
   const bool b_nfast = (d.b_n == 1);
   const float sa = d.conj_a ? -1.f : 1.f;
   const float sb = d.conj_b ? -1.f : 1.f;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
       const int m = m0 + mm, k = k0 + kk;
       float re = 0.f, im = 0.f;
       if (m < d.M && k < K) {
-        const int64_t off = row_off(m, d.M2, d.a_m, d.a_m2) + koff(k, d.K2, d.a_k1, d.a_k2);
+        const int64_t off = ROW_A(d, m) + koff(k, d.K2, d.a_k1, d.a_k2);
         re = A[off];
         im = sa * A[off + d.plane_a];
       }
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= d.N) continue;
-      const int64_t off = row_off(m, d.M2, d.c_m, d.c_m2) + (int64_t)n * d.c_n;
+      const int64_t off = ROW_C(d, m) + (int64_t)n * d.c_n;
       if (d.accumulate) {
         C[off] += accr[i][j];
         C[off + d.plane_c] += acci[i][j];
@@ -186,8 +187,9 @@ __device__ double block_sum(double v, double* sh) {
   return sh[0];
 }
 
-__global__ void normalise_kernel(const float* raw, float* msg, int chi,
-                                 unsigned long long* res_bits, int* flags) {
+// Large chi: the transposed entry is read from global memory.
+__global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
+                                      unsigned long long* res_bits, int* flags) {
   __shared__ double sh[32];
   const int64_t n2 = (int64_t)chi * chi;
   const float* r = raw + blockIdx.x * 2 * n2;
@@ -213,26 +215,140 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
     const double hi = 0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]) * inv;
     const double er = hr - (double)m[idx], ei = hi - (double)m[n2 + idx];
     dd += er * er + ei * ei;
+    m[idx] = (float)hr;
+    m[n2 + idx] = (float)hi;
   }
   dd = block_sum(dd, sh);
-  // every thread has read m for the residual before anyone overwrites it
-  __syncthreads();
-  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
-    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    m[idx] = (float)(0.5 * ((double)r[idx] + (double)r[(int64_t)j * chi + i]) * inv);
-    m[n2 + idx] = (float)(0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]) * inv);
-  }
   if (threadIdx.x == 0) {
     const double res = sqrt(dd);
     atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
   }
 }
+
+// The raw message is staged in shared memory (coalesced loads), so that the
+// transposed entry needed by the Hermitisation is a shared-memory read.
+__global__ void normalise_kernel(const float* raw, float* msg, int chi,
+                                 unsigned long long* res_bits, int* flags, float* mrt) {
+  __shared__ double sh[32];
+  extern __shared__ float sraw[];  // 2 chi^2: re plane, im plane
+  const int64_t n2 = (int64_t)chi * chi;
+  const float* r = raw + blockIdx.x * 2 * n2;
+  float* m = msg + blockIdx.x * 2 * n2;
+  for (int64_t idx = threadIdx.x; idx < 2 * n2; idx += blockDim.x) sraw[idx] = r[idx];
+  __syncthreads();
+  double ss = 0.0;
+  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
+    const double hr = 0.5 * ((double)sraw[idx] + (double)sraw[(int64_t)j * chi + i]);
+    const double hi = 0.5 * ((double)sraw[n2 + idx] - (double)sraw[n2 + (int64_t)j * chi + i]);
+    ss += hr * hr + hi * hi;
+  }
+  ss = block_sum(ss, sh);
+  const double nrm = sqrt(ss);
+  if (!(nrm > 0.0) || !isfinite(nrm)) {
+    if (threadIdx.x == 0) atomicOr(flags, 1);
+    return;
+  }
+  const double inv = 1.0 / nrm;
+  double dd = 0.0;
+  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
+    const double hr = 0.5 * ((double)sraw[idx] + (double)sraw[(int64_t)j * chi + i]) * inv;
+    const double hi = 0.5 * ((double)sraw[n2 + idx] - (double)sraw[n2 + (int64_t)j * chi + i]) * inv;
+    const double er = hr - (double)m[idx], ei = hi - (double)m[n2 + idx];
+    dd += er * er + ei * ei;
+    m[idx] = (float)hr;
+    m[n2 + idx] = (float)hi;
+    if (mrt) {
+      // realified transpose: row (t, n), column (s, k) of a [2chi][2chi] matrix;
+      // the message element [k][n] = (i, j) goes to (0,j)(0,i), (1,j)(1,i) as re,
+      // (1,j)(0,i) as +im and (0,j)(1,i) as -im
+      float* q = mrt + (int64_t)blockIdx.x * 4 * n2;
+      const int64_t w = 2 * chi;
+      q[(int64_t)j * w + i] = (float)hr;
+      q[(int64_t)(chi + j) * w + chi + i] = (float)hr;
+      q[(int64_t)(chi + j) * w + i] = (float)hi;
+      q[(int64_t)j * w + chi + i] = (float)-hi;
+    }
+  }
+  dd = block_sum(dd, sh);
+  if (threadIdx.x == 0) {
+    const double res = sqrt(dd);
+    atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
+  }
+}
+
+// Realified transposed copies (see GemmDesc::b_pre).
+__global__ void realify_kernel(const float* src, int64_t stride, float* dst, int chi) {
+  const int64_t n2 = (int64_t)chi * chi;
+  const float* a = src + blockIdx.y * stride;
+  float* q = dst + (int64_t)blockIdx.y * 4 * n2;
+  const int64_t w = 2 * chi;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n2;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);  // element [k = i][n = j]
+    const float re = a[idx], im = a[n2 + idx];
+    q[(int64_t)j * w + i] = re;
+    q[(int64_t)(chi + j) * w + chi + i] = re;
+    q[(int64_t)(chi + j) * w + i] = im;
+    q[(int64_t)j * w + chi + i] = -im;
+  }
+}
+
+// TA[pl][p][rest][l0] = T[pl][p][l0][rest]: one CTA row per (site, plane, p, l0)
+// block of `rest` = chi^(d-1) contiguous elements.
+__global__ void first_leg_last_kernel(const float* T, float* TA, const int64_t* site_off, int d,
+                                      int chi, int64_t rest) {
+  const int site = blockIdx.y;
+  const int64_t len = rest * chi;  // chi^d
+  const float* src = T + site_off[site];
+  float* dst = TA + site_off[site];
+  const int blk = blockIdx.x;      // (plane, p, l0) in 0 .. 4 chi
+  const int l0 = blk % chi;
+  const int pp = blk / chi;        // plane * 2 + p
+  const float* s = src + (int64_t)pp * len + (int64_t)l0 * rest;
+  float* q = dst + (int64_t)pp * len + l0;
+  for (int64_t r = threadIdx.x; r < rest; r += blockDim.x) q[r * chi] = s[r];
+}
 }  // namespace
 
+cudaError_t launch_realify(const float* src, int64_t src_stride, float* dst, int n, int chi,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t n2 = (int64_t)chi * chi;
+  int64_t bx = (n2 + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid((unsigned)bx, n);
+  realify_kernel<<<grid, 256, 0, s>>>(src, src_stride, dst, chi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site_off, int n_sites,
+                                  int d, int chi, cudaStream_t s) {
+  if (n_sites <= 0 || d < 2) return cudaSuccess;
+  int64_t rest = 1;
+  for (int i = 1; i < d; ++i) rest *= chi;
+  dim3 grid(4 * chi, n_sites);
+  first_leg_last_kernel<<<grid, 128, 0, s>>>(T, TA, site_off, d, chi, rest);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
-                             unsigned long long* res_bits, int* flags, cudaStream_t s) {
+                             unsigned long long* res_bits, int* flags, cudaStream_t s, float* mrt) {
   if (n_msgs <= 0) return cudaSuccess;
-  normalise_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags);
+  const size_t sm = sizeof(float) * 2 * (size_t)chi * chi;
+  if (sm > 200 * 1024) {
+    normalise_gmem_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !mrt) return e;
+    return launch_realify(msg, 2 * (int64_t)chi * chi, mrt, n_msgs, chi, s);
+  }
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(normalise_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  normalise_kernel<<<n_msgs, 256, sm, s>>>(raw, msg, chi, res_bits, flags, mrt);
   return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ constexpr int kStages = 3;
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 128;
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kBatch = 8;                        // 16-byte loads in flight per producer thread
 
 struct TcSmem {
   static constexpr int kA = kTM * kRowBytes;   // 16 KB per stage
@@ -186,7 +187,7 @@ __device__ __forceinline__ float load_a(const GemmDesc& d, const TcArgs& t, cons
   if (t.quad) { s = mr >= d.M; m = mr - s * d.M; k = kr; }
   else { s = kr >= K; k = kr - s * K; m = mr; }
   const int64_t off =
-      row_off(m, d.M2, d.a_m, d.a_m2) + koff(k, d.K2, d.a_k1, d.a_k2) + (s ? d.plane_a : 0);
+      ROW_A(d, m) + koff(k, d.K2, d.a_k1, d.a_k2) + (s ? d.plane_a : 0);
   float v = __ldg(A + off);
   if (!t.quad && s && d.conj_a) v = -v;
   return v;
@@ -240,7 +241,7 @@ __device__ __forceinline__ void store_elem(unsigned char* tile, int row, int kk,
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs t) {
+__global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs t) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // align the dynamic buffer to 1024 bytes (swizzle atoms)
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -297,18 +298,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs
                       (t.kr % kelems == 0);
     const bool a_kvec = kvec && d.a_k2 == 1 && (d.a_m % 4 == 0) && (d.a_k1 % 4 == 0) &&
                         (d.plane_a % 4 == 0) && (d.a_in % 4 == 0) &&
-                        (d.M2 <= 1 || d.a_m2 % 4 == 0);
-    // A rows contiguous: four consecutive rows m..m+3 (same m1, same plane) are adjacent
+                        (d.M2 <= 1 || d.a_m2 % 4 == 0) && (d.M3 <= 1 || d.a_m3 % 4 == 0);
+    // A rows contiguous: four consecutive rows m..m+3 (same upper row levels, same
+    // plane) are adjacent
+    bool a_rows4;
+    if (d.M3 > 1) a_rows4 = d.a_m3 == 1 && d.M3 % 4 == 0 && d.a_m % 4 == 0 && d.a_m2 % 4 == 0;
+    else if (d.M2 > 1) a_rows4 = d.a_m2 == 1 && d.M2 % 4 == 0 && d.a_m % 4 == 0;
+    else a_rows4 = d.a_m == 1;
     const bool a_mvec = !a_kvec && (d.M % 4 == 0) && (d.a_k1 % 4 == 0) && (d.a_k2 % 4 == 0) &&
-                        (d.plane_a % 4 == 0) && (d.a_in % 4 == 0) &&
-                        ((d.M2 > 1) ? (d.a_m2 == 1 && d.M2 % 4 == 0 && d.a_m % 4 == 0)
-                                    : (d.a_m == 1));
+                        (d.plane_a % 4 == 0) && (d.a_in % 4 == 0) && a_rows4;
+    // B K-contiguous: the closes' long operand, or the realified transposed small
+    // operand of a b_pre descriptor (read as a plain real matrix, no signs)
     const bool b_kvec = kvec && d.b_k2 == 1 && (d.b_n % 4 == 0) && (d.b_k1 % 4 == 0) &&
-                        (d.plane_b % 4 == 0) && (d.b_in % 4 == 0) && t.quad;
+                        (d.plane_b % 4 == 0) && (d.b_in % 4 == 0) && (t.quad || d.b_pre);
     const bool b_nvec = !b_kvec && d.b_n == 1 && (d.N % 4 == 0) && (d.b_k1 % 4 == 0) &&
                         (d.b_k2 % 4 == 0) && (d.plane_b % 4 == 0) && (d.b_in % 4 == 0) &&
                         (t.tn % 4 == 0) && (n0 % 4 == 0);
-    const bool a_kfast = d.a_k2 == 1 && !(d.M2 > 1 && d.a_m2 == 1);
+    const bool a_kfast = d.a_k2 == 1 && !(d.M2 > 1 && d.M3 <= 1 && d.a_m2 == 1) &&
+                         !(d.M3 > 1 && d.a_m3 == 1);
     const bool b_nfast = d.b_n == 1;
     const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
     for (int kt = 0; kt < ntiles; ++kt) {
@@ -319,41 +326,70 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs
       unsigned char* ta = sA + s * TcSmem::kA;
       unsigned char* tb = sB + s * TcSmem::kB;
       const int k0 = kbeg + kt * kelems;
+      // Each path issues kBatch 16-byte loads per thread before converting and
+      // storing them, so that every producer thread keeps kBatch loads in flight.
       if (a_kvec && aligned) {
         // A: K-contiguous; the whole tile lies in one plane (s) and one K2 run
         int sa, kloc;
         if (t.quad) { sa = 0; kloc = k0; } else { sa = k0 >= K; kloc = k0 - sa * K; }
         const int64_t kbase = koff(kloc, d.K2, d.a_k1, d.a_k2);
-        for (int c = pt; c < kTM * (kelems / 4); c += 128) {
-          const int row = c / (kelems / 4), q = c % (kelems / 4);
-          const int mr = m0 + row;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (mr < t.mr && k0 + q * 4 < kend) {
-            int m = mr, splane = sa;
-            if (t.quad) { splane = mr >= d.M; m = mr - splane * d.M; }
-            v = __ldg(reinterpret_cast<const float4*>(A + row_off(m, d.M2, d.a_m, d.a_m2) +
-                                                      kbase + q * 4 + (splane ? d.plane_a : 0)));
-            if (!t.quad && splane && d.conj_a) { v.x = -v.x; v.y = -v.y; v.z = -v.z; v.w = -v.w; }
-          }
-          store_k4(ta, row, q * 4, v, t.bf16);
-        }
-      } else if (a_mvec && aligned) {
-        for (int c = pt; c < (kTM / 4) * kelems; c += 128) {
-          const int rq = c % (kTM / 4), kk = c / (kTM / 4);
-          const int row = rq * 4, mr = m0 + row, kr = k0 + kk;
-          float v4[4] = {0.f, 0.f, 0.f, 0.f};
-          if (mr < t.mr && kr < kend) {
-            int sp, m, k;
-            if (t.quad) { sp = mr >= d.M; m = mr - sp * d.M; k = kr; }
-            else { sp = kr >= K; k = kr - sp * K; m = mr; }
-            const float4 v = __ldg(reinterpret_cast<const float4*>(
-                A + row_off(m, d.M2, d.a_m, d.a_m2) + koff(k, d.K2, d.a_k1, d.a_k2) +
-                (sp ? d.plane_a : 0)));
-            const float sign = (!t.quad && sp && d.conj_a) ? -1.f : 1.f;
-            v4[0] = sign * v.x; v4[1] = sign * v.y; v4[2] = sign * v.z; v4[3] = sign * v.w;
+        const int qpr = kelems / 4, total = kTM * qpr;
+        for (int base = 0; base < total; base += 128 * kBatch) {
+          float4 v[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            const int row = c / qpr, q = c - (c / qpr) * qpr;
+            const int mr = m0 + row;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < total && mr < t.mr && k0 + q * 4 < kend) {
+              int m = mr, splane = sa;
+              if (t.quad) { splane = mr >= d.M; m = mr - splane * d.M; }
+              v[u] = __ldg(reinterpret_cast<const float4*>(A + ROW_A(d, m) +
+                                                           kbase + q * 4 + (splane ? d.plane_a : 0)));
+              if (!t.quad && splane && d.conj_a) {
+                v[u].x = -v[u].x; v[u].y = -v[u].y; v[u].z = -v[u].z; v[u].w = -v[u].w;
+              }
+            }
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) store_elem(ta, row + u, kk, v4[u], t.bf16);
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            if (c < total) store_k4(ta, c / qpr, (c - (c / qpr) * qpr) * 4, v[u], t.bf16);
+          }
+        }
+      } else if (a_mvec && aligned) {
+        const int total = (kTM / 4) * kelems;
+        for (int base = 0; base < total; base += 128 * kBatch) {
+          float4 v[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            const int rq = c % (kTM / 4), kk = c / (kTM / 4);
+            const int mr = m0 + rq * 4, kr = k0 + kk;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < total && mr < t.mr && kr < kend) {
+              int sp, m, k;
+              if (t.quad) { sp = mr >= d.M; m = mr - sp * d.M; k = kr; }
+              else { sp = kr >= K; k = kr - sp * K; m = mr; }
+              v[u] = __ldg(reinterpret_cast<const float4*>(
+                  A + ROW_A(d, m) + koff(k, d.K2, d.a_k1, d.a_k2) +
+                  (sp ? d.plane_a : 0)));
+              if (!t.quad && sp && d.conj_a) {
+                v[u].x = -v[u].x; v[u].y = -v[u].y; v[u].z = -v[u].z; v[u].w = -v[u].w;
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            if (c >= total) continue;
+            const int row = (c % (kTM / 4)) * 4, kk = c / (kTM / 4);
+            store_elem(ta, row, kk, v[u].x, t.bf16);
+            store_elem(ta, row + 1, kk, v[u].y, t.bf16);
+            store_elem(ta, row + 2, kk, v[u].z, t.bf16);
+            store_elem(ta, row + 3, kk, v[u].w, t.bf16);
+          }
         }
       } else {
         for (int i = pt; i < kTM * kelems; i += 128) {
@@ -367,39 +403,65 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs
       }
       if (b_kvec && aligned) {
         const int64_t kbase = koff(k0, d.K2, d.b_k1, d.b_k2);
-        for (int c = pt; c < t.tn * (kelems / 4); c += 128) {
-          const int row = c / (kelems / 4), q = c % (kelems / 4);
-          const int nr = n0 + row;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (nr < t.nr && k0 + q * 4 < kend) {
-            const int tt = nr >= d.N;
-            const int n = nr - tt * d.N;
-            v = __ldg(reinterpret_cast<const float4*>(B + (int64_t)n * d.b_n + kbase + q * 4 +
-                                                      (tt ? d.plane_b : 0)));
+        const int qpr = kelems / 4, total = t.tn * qpr;
+        for (int base = 0; base < total; base += 128 * kBatch) {
+          float4 v[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            const int row = c / qpr, q = c - (c / qpr) * qpr;
+            const int nr = n0 + row;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < total && nr < t.nr && k0 + q * 4 < kend) {
+              const int tt = nr >= d.N;
+              const int n = nr - tt * d.N;
+              v[u] = __ldg(reinterpret_cast<const float4*>(B + (int64_t)n * d.b_n + kbase + q * 4 +
+                                                           (tt ? d.plane_b : 0)));
+            }
           }
-          store_k4(tb, row, q * 4, v, t.bf16);
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            if (c < total) store_k4(tb, c / qpr, (c - (c / qpr) * qpr) * 4, v[u], t.bf16);
+          }
         }
       } else if (b_nvec && aligned) {
         // B: N-contiguous; four consecutive rows nr share (t, s, k)
-        for (int c = pt; c < (t.tn / 4) * kelems; c += 128) {
-          const int rq = c % (t.tn / 4), kk = c / (t.tn / 4);
-          const int row = rq * 4, nr = n0 + row, kr = k0 + kk;
-          float v4[4] = {0.f, 0.f, 0.f, 0.f};
-          if (nr < t.nr && kr < kend) {
-            const int tt = nr >= d.N;
-            const int n = nr - tt * d.N;
-            int sk = 0, k = kr;
-            if (!t.quad) { sk = kr >= K; k = kr - sk * K; }
-            const int64_t base = (int64_t)n * d.b_n + koff(k, d.K2, d.b_k1, d.b_k2);
-            float sign = 1.f;
-            int64_t off = base;
-            if (t.quad) { off += tt ? d.plane_b : 0; }
-            else if (sk != tt) { off += d.plane_b; sign = (d.conj_b ? -1.f : 1.f) * (sk == 0 ? 1.f : -1.f); }
-            const float4 v = __ldg(reinterpret_cast<const float4*>(B + off));
-            v4[0] = sign * v.x; v4[1] = sign * v.y; v4[2] = sign * v.z; v4[3] = sign * v.w;
+        const int total = (t.tn / 4) * kelems;
+        for (int base = 0; base < total; base += 128 * kBatch) {
+          float4 v[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            const int rq = c % (t.tn / 4), kk = c / (t.tn / 4);
+            const int nr = n0 + rq * 4, kr = k0 + kk;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < total && nr < t.nr && kr < kend) {
+              const int tt = nr >= d.N;
+              const int n = nr - tt * d.N;
+              int sk = 0, k = kr;
+              if (!t.quad) { sk = kr >= K; k = kr - sk * K; }
+              int64_t off = (int64_t)n * d.b_n + koff(k, d.K2, d.b_k1, d.b_k2);
+              float sign = 1.f;
+              if (t.quad) { off += tt ? d.plane_b : 0; }
+              else if (sk != tt) {
+                off += d.plane_b;
+                sign = (d.conj_b ? -1.f : 1.f) * (sk == 0 ? 1.f : -1.f);
+              }
+              v[u] = __ldg(reinterpret_cast<const float4*>(B + off));
+              v[u].x *= sign; v[u].y *= sign; v[u].z *= sign; v[u].w *= sign;
+            }
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) store_elem(tb, row + u, kk, v4[u], t.bf16);
+          for (int u = 0; u < kBatch; ++u) {
+            const int c = base + u * 128 + pt;
+            if (c >= total) continue;
+            const int row = (c % (t.tn / 4)) * 4, kk = c / (t.tn / 4);
+            store_elem(tb, row, kk, v[u].x, t.bf16);
+            store_elem(tb, row + 1, kk, v[u].y, t.bf16);
+            store_elem(tb, row + 2, kk, v[u].z, t.bf16);
+            store_elem(tb, row + 3, kk, v[u].w, t.bf16);
+          }
         }
       } else {
         for (int i = pt; i < t.tn * kelems; i += 128) {
@@ -454,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs
         const int nb = n0 + c0;
         const int tt0 = nb >= d.N;
         if (d.c_n == 1 && !d.accumulate && nb + 32 <= t.nr && (nb - tt0 * d.N) + 32 <= d.N) {
-          float* p = C + row_off(mr, d.M2, d.c_m, d.c_m2) + (nb - tt0 * d.N) + (tt0 ? d.plane_c : 0);
+          float* p = C + ROW_C(d, mr) + (nb - tt0 * d.N) + (tt0 ? d.plane_c : 0);
           if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4)
@@ -468,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs
           if (nr >= t.nr) break;
           const int tt = nr >= d.N;
           const int n = nr - tt * d.N;
-          float* p = C + row_off(mr, d.M2, d.c_m, d.c_m2) + (int64_t)n * d.c_n + (tt ? d.plane_c : 0);
+          float* p = C + ROW_C(d, mr) + (int64_t)n * d.c_n + (tt ? d.plane_c : 0);
           if (d.accumulate) *p += v[j]; else *p = v[j];
         }
       }
@@ -502,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmDesc d, TcArgs
           q[(int64_t)m * N + n] = cr;
           q[(int64_t)M * N + (int64_t)m * N + n] = ci;
         } else if (valid) {
-          float* p = C + row_off(m, d.M2, d.c_m, d.c_m2) + (int64_t)n * d.c_n;
+          float* p = C + ROW_C(d, m) + (int64_t)n * d.c_n;
           if (d.accumulate) { p[0] += cr; p[d.plane_c] += ci; }
           else { p[0] = cr; p[d.plane_c] = ci; }
         }
@@ -534,7 +596,7 @@ __global__ void tc_reduce_kernel(GemmDesc d, const float* part, int splits) {
       cr += q[idx];
       ci += q[(int64_t)M * N + idx];
     }
-    float* p = C + row_off(m, d.M2, d.c_m, d.c_m2) + (int64_t)n * d.c_n;
+    float* p = C + ROW_C(d, m) + (int64_t)n * d.c_n;
     if (d.accumulate) { p[0] += cr; p[d.plane_c] += ci; }
     else { p[0] = cr; p[d.plane_c] = ci; }
   }
@@ -548,7 +610,7 @@ size_t tc_smem_bytes() { return TcSmem::kBytes + 1024; }
 // M, N small (2M <= 128), else realified-B form.
 bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {
   const int64_t K = (int64_t)d.K1 * d.K2;
-  *quad = (2 * d.M <= kTM && 2 * d.N <= kTN && K >= 4 * d.M) ? 1 : 0;
+  *quad = (2 * d.M <= kTM && 2 * d.N <= kTN && !d.b_pre) ? 1 : 0;
   *splits = 1;
   *part_floats = 0;
   if (*quad) {
@@ -586,6 +648,9 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tc_smem_bytes());
+    if (e != cudaSuccess) return e;
+    // two CTAs per SM: ask for the largest shared-memory carveout
+    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
