@@ -2,10 +2,9 @@
 //
 // Same inputs and outputs as the FP64 solve in solve.cu (open-p environments
 // of both sides of each gate edge in; per-p leg matrices D, the new bond
-// spectrum and the gate-edge messages out), organised so that the O(chi^3)
-// iterative part (the one-sided Jacobi sweeps) runs from shared memory on the
-// FP32 pipes.  The Gram factorisations, norms, the spectrum and its
-// normalisation are FP64.
+// spectrum and the gate-edge messages out), organised so that every O(chi^3)
+// step runs from shared memory on the FP32 pipes.  Norms, the spectrum and its
+// normalisation are accumulated in FP64.
 //
 // The gate exp(s i pi/4 ZZ) is split on the projectors of v's physical index:
 // exp(s i pi/4 ZZ) = sum_p |p><p| (x) B_p, B_p = exp(s i pi/4 s_p Z), s_0 = +1,
@@ -14,8 +13,8 @@
 // Gram matrix G_v = diag(conj N_0, conj N_1); on the w side
 // G_w[(e,k), (e',k')] = sum_q conj(b_k(q)) b_k'(q) conj(N_q^w)[e, e'] with
 // b_k(q) = exp(s i pi/4 s_k s_q).  Steps per edge (one CTA):
-//   1. pivoted Cholesky (FP64) of the two chi x chi blocks of G_v and of G_w
-//      (2chi): P^T G P = L L^H, so G = R^H R with R = L^H P^T;
+//   1. pivoted Cholesky of the two chi x chi blocks of G_v and of G_w (2chi):
+//      P^T G P = L L^H, so G = R^H R with R = L^H P^T;
 //   2. K^T = R_w R_v^T (the bond matrix K = R_v R_w^T, transposed);
 //   3. one-sided Jacobi on the columns of K (rows of K^T) until every pair is
 //      orthogonal to FP32 precision: K V = U diag(sigma), with no squaring of
@@ -35,9 +34,6 @@ namespace {
 
 constexpr int kThreads = 512;
 
-__device__ __forceinline__ int64_t solve_work_doubles_dev(int chi) {
-  return (int64_t)12 * (2 * chi) * (2 * chi);
-}
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChi = 64;
 constexpr float kOrthTol = 2e-6f;
@@ -47,7 +43,6 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cconjf(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -61,93 +56,88 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-struct zd { double x, y; };
-__device__ __forceinline__ zd zmul(zd a, zd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ zd zconj(zd a) { return {a.x, -a.y}; }
-
-// FP64 pivoted Cholesky of the Hermitian PSD m x m matrix A (row stride ld,
-// full storage) in place: afterwards A's lower triangle holds L with
-// P^T A P = L L^H, perm[t] = original index of pivot t, and *rank the number of
-// pivots above rel_tol * (largest initial diagonal); everything outside the
-// first `rank` columns of the lower triangle is zeroed.  The trailing update
-// keeps the full Hermitian block current, so each pivot's row and column
-// exchange reads current values.  A may live in shared or global memory.  colk: m complex doubles of shared scratch holding
-// the current column of L for the trailing update.
-__device__ void pivoted_cholesky64(zd* A, int m, int ld, int* perm, double rel_tol, int* rank,
-                                   double* red_v, int* red_i, double* dmax0, zd* colk) {
+// Pivoted Cholesky of the Hermitian PSD m x m matrix A (row stride ld, full
+// storage) in place, FP32 in shared memory: afterwards A's lower triangle holds
+// L with P^T A P = L L^H, perm[t] = original index of pivot t, and *rank the
+// number of pivots above rel_tol * (largest initial diagonal); everything
+// outside the first `rank` columns of the lower triangle is zeroed.  The
+// trailing update keeps the full Hermitian block current, so each pivot's row
+// and column exchange reads current values.
+__device__ void pivoted_cholesky32(float2* A, int m, int ld, int* perm, float rel_tol, int* rank,
+                                   float* red_v, int* red_i, float* dmax0, float2* colk) {
   const int tid = threadIdx.x;
   for (int i = tid; i < m; i += blockDim.x) perm[i] = i;
   __syncthreads();
   int r = m;
   for (int k = 0; k < m; ++k) {
-    double best = -1.0;
+    float best = -1.f;
     int bi = k;
     for (int i = k + tid; i < m; i += blockDim.x) {
-      const double d = A[(int64_t)i * ld + i].x;
+      const float d = A[i * ld + i].x;
       if (d > best) { best = d; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
     if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
     __syncthreads();
     if (tid == 0) {
-      double b = red_v[0];
+      float b = red_v[0];
       int ii = red_i[0];
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
         if (red_v[w] > b || (red_v[w] == b && red_i[w] < ii)) { b = red_v[w]; ii = red_i[w]; }
       red_v[0] = b;
       red_i[0] = ii;
-      if (k == 0) *dmax0 = b > 0.0 ? b : 0.0;
+      if (k == 0) *dmax0 = b > 0.f ? b : 0.f;
     }
     __syncthreads();
-    const double pv = red_v[0];
+    const float pv = red_v[0];
     const int piv = red_i[0];
-    const double d0 = *dmax0;
+    const float d0 = *dmax0;
     __syncthreads();
-    if (!(d0 > 0.0) || !(pv > rel_tol * d0)) { r = k; break; }
+    if (!(d0 > 0.f) || !(pv > rel_tol * d0)) { r = k; break; }
     if (piv != k) {
       for (int j = tid; j < m; j += blockDim.x) {
-        const zd t = A[(int64_t)k * ld + j];
-        A[(int64_t)k * ld + j] = A[(int64_t)piv * ld + j];
-        A[(int64_t)piv * ld + j] = t;
+        const float2 t = A[k * ld + j];
+        A[k * ld + j] = A[piv * ld + j];
+        A[piv * ld + j] = t;
       }
       __syncthreads();
       for (int i = tid; i < m; i += blockDim.x) {
-        const zd t = A[(int64_t)i * ld + k];
-        A[(int64_t)i * ld + k] = A[(int64_t)i * ld + piv];
-        A[(int64_t)i * ld + piv] = t;
+        const float2 t = A[i * ld + k];
+        A[i * ld + k] = A[i * ld + piv];
+        A[i * ld + piv] = t;
       }
       if (tid == 0) { const int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t; }
       __syncthreads();
     }
-    const double d = sqrt(A[(int64_t)k * ld + k].x);
-    const double inv = 1.0 / d;
+    const float d = sqrtf(A[k * ld + k].x);
+    const float inv = 1.f / d;
     __syncthreads();
     for (int i = k + 1 + tid; i < m; i += blockDim.x) {
-      const zd a = A[(int64_t)i * ld + k];
-      const zd l = {a.x * inv, a.y * inv};
-      A[(int64_t)i * ld + k] = l;
+      const float2 a = A[i * ld + k];
+      const float2 l = make_float2(a.x * inv, a.y * inv);
+      A[i * ld + k] = l;
       colk[i] = l;
     }
     __syncthreads();
-    if (tid == 0) A[(int64_t)k * ld + k] = {d, 0.0};
+    if (tid == 0) A[k * ld + k] = make_float2(d, 0.f);
     const int rem = m - k - 1;
     for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
       const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-      const zd p = zmul(colk[i], zconj(colk[j]));
-      zd a = A[(int64_t)i * ld + j];
+      const float2 p = cmulf(colk[i], cconjf(colk[j]));
+      float2 a = A[i * ld + j];
       a.x -= p.x;
       a.y -= p.y;
-      A[(int64_t)i * ld + j] = a;
+      A[i * ld + j] = a;
     }
     __syncthreads();
   }
   for (int idx = tid; idx < m * m; idx += blockDim.x) {
     const int i = idx / m, j = idx % m;
-    if (j > i || j >= r) A[(int64_t)i * ld + j] = {0.0, 0.0};
+    if (j > i || j >= r) A[i * ld + j] = make_float2(0.f, 0.f);
   }
   if (tid == 0) *rank = r;
   __syncthreads();
@@ -168,7 +158,7 @@ struct Smem {
   double* sig;     // n
   double* scal;    // 4
   double* red_d;   // 32
-  zd* colk;        // n
+  float2* colk;    // n
 };
 
 __device__ Smem carve(unsigned char* base, int chi) {
@@ -180,7 +170,7 @@ __device__ Smem carve(unsigned char* base, int chi) {
   s.sig = reinterpret_cast<double*>(p); p += sizeof(double) * n;
   s.scal = reinterpret_cast<double*>(p); p += sizeof(double) * 4;
   s.red_d = reinterpret_cast<double*>(p); p += sizeof(double) * 32;
-  s.colk = reinterpret_cast<zd*>(p); p += sizeof(zd) * n;
+  s.colk = reinterpret_cast<float2*>(p); p += sizeof(float2) * n;
   s.perm_w = reinterpret_cast<int*>(p); p += sizeof(int) * n;
   s.perm_v = reinterpret_cast<int*>(p); p += sizeof(int) * 2 * chi;
   s.src = reinterpret_cast<int*>(p); p += sizeof(int) * n;
@@ -205,51 +195,49 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   const float* gw = gv + 4 * c2;
   const float sg = (float)a.sign;
 
-  // 1. Gram matrices in FP64.  G_v blocks conj(N_p^v) in shared memory (they
-  //    fit in the space X takes later); G_w from conj(N_q^w) in this edge's
-  //    global workspace (L2-resident).
-  zd* Gv64 = reinterpret_cast<zd*>(X);                    // 2 chi^2 zd == n^2 float2
-  zd* Gw64 = reinterpret_cast<zd*>(a.work + (int64_t)edge * solve_work_doubles_dev(chi));
+  // 1. Gram matrices: G_v blocks conj(N_p^v) in Lv, G_w from conj(N_q^w) in X.
   for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
     const int p = idx / (chi * chi), o = idx % (chi * chi);
-    Gv64[idx] = {(double)gv[p * 2 * c2 + o], -(double)gv[p * 2 * c2 + c2 + o]};
+    s.Lv[idx] = make_float2(gv[p * 2 * c2 + o], -gv[p * 2 * c2 + c2 + o]);
   }
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx % n;
     const int ki = i / chi, ei = i % chi, kj = j / chi, ej = j % chi;
     const int64_t o = (int64_t)ei * chi + ej;
-    const zd g0 = {(double)gw[o], -(double)gw[c2 + o]};
-    const zd g1 = {(double)gw[2 * c2 + o], -(double)gw[3 * c2 + o]};
-    zd v;
+    const float2 g0 = make_float2(gw[o], -gw[c2 + o]);
+    const float2 g1 = make_float2(gw[2 * c2 + o], -gw[3 * c2 + o]);
+    float2 v;
     if (ki == kj) {
-      v = {g0.x + g1.x, g0.y + g1.y};
+      v = make_float2(g0.x + g1.x, g0.y + g1.y);
     } else {
       // conj(b_ki(q)) b_kj(q) = exp(s i pi/4 (s_kj - s_ki) s_q): (0,1) -> -s i s_q,
       // (1,0) -> +s i s_q, so the block is -+ s i (G_0 - G_1)
-      const zd d = {g0.x - g1.x, g0.y - g1.y};
-      const double f = (ki == 0) ? -(double)sg : (double)sg;
-      v = {-f * d.y, f * d.x};
+      const float2 d = make_float2(g0.x - g1.x, g0.y - g1.y);
+      const float f = (ki == 0) ? -sg : sg;
+      v = make_float2(-f * d.y, f * d.x);
     }
-    Gw64[idx] = v;
+    X[idx] = v;
   }
   __syncthreads();
-  const double ctol = 1e-13;
-  double* dmax0d = s.scal + 3;
-  pivoted_cholesky64(Gv64, chi, chi, s.perm_v, ctol, &s.rank[0], s.red_d, s.red_i, dmax0d, s.colk);
-  pivoted_cholesky64(Gv64 + chi * chi, chi, chi, s.perm_v + chi, ctol, &s.rank[1], s.red_d,
-                     s.red_i, dmax0d, s.colk);
-  for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x)
-    s.Lv[idx] = make_float2((float)Gv64[idx].x, (float)Gv64[idx].y);
-  __syncthreads();
-  pivoted_cholesky64(Gw64, n, n, s.perm_w, ctol, &s.rank[2], s.red_d, s.red_i, dmax0d, s.colk);
+  const float ctol = 1e-7f;
+  float2* colk = reinterpret_cast<float2*>(s.colk);
+  pivoted_cholesky32(s.Lv, chi, chi, s.perm_v, ctol, &s.rank[0], s.red_v, s.red_i, s.dmax0, colk);
+  pivoted_cholesky32(s.Lv + chi * chi, chi, chi, s.perm_v + chi, ctol, &s.rank[1], s.red_v,
+                     s.red_i, s.dmax0, colk);
+  pivoted_cholesky32(X, n, n, s.perm_w, ctol, &s.rank[2], s.red_v, s.red_i, s.dmax0, colk);
 
-  // 2. K^T = R_w R_v^T.  First X[j][t] = conj(L_w[t][j]) (FP32), so that row j
-  //    of X holds R_w[j][perm_w[t]] at column t.  Then with c = perm_b[t'] (block b):
+  // 2. K^T = R_w R_v^T.  First X <- conj(L_w^T) so that row j of X holds
+  //    R_w[j][perm_w[t]] at column t.  Then with c = perm_b[t'] (block b):
   //    K^T[j][(b, i)] = sum_t' X[j][pinv_w(b chi + perm_b[t'])] conj(L_b[t'][i]).
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int j = idx / n, t = idx % n;
-    const zd l = Gw64[(int64_t)t * n + j];
-    X[idx] = make_float2((float)l.x, (float)-l.y);
+    const int i = idx / n, j = idx % n;
+    if (i < j) {
+      const float2 u = X[i * n + j], l = X[j * n + i];
+      X[i * n + j] = cconjf(l);
+      X[j * n + i] = cconjf(u);
+    } else if (i == j) {
+      X[idx] = cconjf(X[idx]);
+    }
   }
   // src[(b, t')] = pinv_w(b chi + perm_b[t'])
   for (int t = tid; t < n; t += blockDim.x) s.src[s.perm_w[t]] = -1 - t;  // temp: pinv_w

@@ -99,6 +99,18 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (zero fill when !valid).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+// Arrive on the mbarrier once this thread's prior cp.async copies have landed.
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -316,6 +328,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
                         (t.tn % 4 == 0) && (n0 % 4 == 0);
     const bool a_kfast = d.a_k2 == 1 && !(d.M2 > 1 && d.M3 <= 1 && d.a_m2 == 1) &&
                          !(d.M3 > 1 && d.a_m3 == 1);
+    const bool a_async = !t.bf16 && a_kvec && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                         !(d.conj_a && !t.quad);
+    const bool b_async = !t.bf16 && b_kvec && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
     const bool b_nfast = d.b_n == 1;
     const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
     for (int kt = 0; kt < ntiles; ++kt) {
@@ -326,9 +341,30 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
       unsigned char* ta = sA + s * TcSmem::kA;
       unsigned char* tb = sB + s * TcSmem::kB;
       const int k0 = kbeg + kt * kelems;
-      // Each path issues kBatch 16-byte loads per thread before converting and
-      // storing them, so that every producer thread keeps kBatch loads in flight.
-      if (a_kvec && aligned) {
+      // TF32 operands whose K index is contiguous are copied with cp.async
+      // straight into their swizzled place (the tensor core reads the FP32 bits
+      // as TF32); the stage's mbarrier then completes when the copies land, so
+      // the producers run ahead by up to kStages stages.  Other operands go
+      // through registers: kBatch 16-byte loads in flight per thread, then
+      // conversion and stores.
+      if (a_async) {
+        int sa, kloc;
+        if (t.quad) { sa = 0; kloc = k0; } else { sa = k0 >= K; kloc = k0 - sa * K; }
+        const int64_t kbase = koff(kloc, d.K2, d.a_k1, d.a_k2);
+        const uint32_t base_s = smem_u32(ta);
+        for (int c = pt; c < kTM * 8; c += 128) {
+          const int row = c >> 3, q = c & 7;
+          const int mr = m0 + row;
+          const bool ok = mr < t.mr && k0 + q * 4 < kend;
+          const float* src = A;
+          if (ok) {
+            int m = mr, splane = sa;
+            if (t.quad) { splane = mr >= d.M; m = mr - splane * d.M; }
+            src = A + ROW_A(d, m) + kbase + q * 4 + (splane ? d.plane_a : 0);
+          }
+          cp_async16(base_s + row * kRowBytes + ((q ^ (row & 7)) << 4), src, ok);
+        }
+      } else if (a_kvec && aligned) {
         // A: K-contiguous; the whole tile lies in one plane (s) and one K2 run
         int sa, kloc;
         if (t.quad) { sa = 0; kloc = k0; } else { sa = k0 >= K; kloc = k0 - sa * K; }
@@ -401,7 +437,22 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
           store_elem(ta, row, kk, v, t.bf16);
         }
       }
-      if (b_kvec && aligned) {
+      if (b_async) {
+        const int64_t kbase = koff(k0, d.K2, d.b_k1, d.b_k2);
+        const uint32_t base_s = smem_u32(tb);
+        for (int c = pt; c < t.tn * 8; c += 128) {
+          const int row = c >> 3, q = c & 7;
+          const int nr = n0 + row;
+          const bool ok = nr < t.nr && k0 + q * 4 < kend;
+          const float* src = B;
+          if (ok) {
+            const int tt = nr >= d.N;
+            const int n = nr - tt * d.N;
+            src = B + (int64_t)n * d.b_n + kbase + q * 4 + (tt ? d.plane_b : 0);
+          }
+          cp_async16(base_s + row * kRowBytes + ((q ^ (row & 7)) << 4), src, ok);
+        }
+      } else if (b_kvec && aligned) {
         const int64_t kbase = koff(k0, d.K2, d.b_k1, d.b_k2);
         const int qpr = kelems / 4, total = t.tn * qpr;
         for (int base = 0; base < total; base += 128 * kBatch) {
@@ -473,8 +524,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
           store_elem(tb, row, kk, v, t.bf16);
         }
       }
-      fence_proxy_async();
-      mbar_arrive(&full[s]);
+      if (!(a_async && b_async)) fence_proxy_async();  // generic-proxy stores of this stage
+      if (a_async || b_async) cp_async_arrive(&full[s]);
+      else mbar_arrive(&full[s]);
     }
   } else if (warp == 0) {
     // ------------------------------------------------------------ MMA issue
@@ -485,6 +537,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
         const bool ok = mbar_wait(&full[s], (kt / kStages) & 1, t.err);
         if (!ok) *abort_flag = 1;
         if (!*abort_flag) {
+          // the stage was written through the generic proxy (cp.async, st.shared);
+          // order those writes before the tensor core's async-proxy reads
+          fence_proxy_async();
           tc_fence_after();
           const uint32_t a0 = smem_u32(sA + s * TcSmem::kA);
           const uint32_t b0 = smem_u32(sB + s * TcSmem::kB);
