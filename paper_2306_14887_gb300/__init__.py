@@ -224,7 +224,9 @@ class TNState:
         g, self._keep = _graph_struct(n, edges, colours)
         cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve)
         if stream is None:
-            stream = torch.cuda.current_stream()
+            # a stream of its own: the library captures its BP sweep as a CUDA
+            # graph, which the legacy default stream does not allow
+            stream = torch.cuda.Stream()
         self._stream = stream
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self._sp = sp

@@ -84,6 +84,9 @@ cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s);
 // set when a device-side wait gave up.
 bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats);
 cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t s);
+// Kernel attributes set once, before any launch or stream capture.
+cudaError_t tc_prepare();
+cudaError_t normalise_prepare(int chi);
 
 // RX-type 2x2 on the physical leg: T[p] <- sum_q U[p][q] T[q] for every site in
 // the list.  site_off: float offset of each site's real plane; len: chi^d

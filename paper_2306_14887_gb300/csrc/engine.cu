@@ -116,6 +116,11 @@ struct tn_handle {
 
   tn_stats stats{};
   double* h_stats = nullptr;  // host copy of solve stats
+  // one BP sweep captured as a CUDA graph (memset of the status words, the
+  // contraction launches, normalisation, read-back of the status words)
+  cudaGraphExec_t sweep_exec = nullptr;
+  double sweep_flops = 0.0, sweep_bytes = 0.0;
+  unsigned long long* h_status = nullptr;  // pinned: [residual bits, flags]
 
   // per-kernel-class timing with CUDA events on the handle's stream
   bool prof_on = false;
@@ -536,6 +541,9 @@ void deg2_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites,
 void build_sweep_plan(tn_handle* h) {
   const HostGraph& g = h->g;
   Plan& P = h->sweep;
+  // All sites of a degree in one launch per chain stage: grouping the sites so
+  // that a group's intermediates stay in L2 costs more in lost parallelism
+  // than it saves in traffic (measured at chi = 64 on 127 qubits).
   const std::vector<int>& s3 = h->sites_by_deg[3];
   for (int which = 0; which < 3; ++which) {
     std::vector<float*> outs;
@@ -823,6 +831,54 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   return check_flags(h, "the truncation solve");
 }
 
+// Enqueue one sweep: clear the status words, contract, normalise (residual and
+// flags accumulate in the status words), copy them to pinned host memory.
+tn_status enqueue_sweep(tn_handle* h) {
+  const int nmsg = 2 * (int)h->g.eu.size();
+  TN_CUDA_TRY(cudaMemsetAsync(h->res_bits, 0, 2 * sizeof(unsigned long long), h->stream));
+  tn_status st = run_plan(h, h->sweep, P_BP);
+  if (st) return st;
+  const int pi = prof_begin(h, P_NORM);
+  TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream,
+                               h->mrt));
+  prof_end(h, pi, 0.0, 3.0 * 8.0 * h->chi * h->chi * nmsg);
+  TN_CUDA_TRY(cudaMemcpyAsync(h->h_status, h->res_bits, 2 * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, h->stream));
+  return TN_OK;
+}
+
+// Capture enqueue_sweep into a graph (once, on a non-default stream).  While
+// profiling, the whole graph is timed as one bp_contract launch.
+tn_status sweep_graph(tn_handle* h, bool* use) {
+  *use = false;
+  if (!h->sweep_exec) {
+    if (!h->stream) return TN_OK;  // the legacy default stream cannot be captured
+    cudaGraph_t graph = nullptr;
+    const bool prof = h->prof_on;
+    h->prof_on = false;
+    TN_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t launches = h->stats.kernel_launches;
+    tn_status st = enqueue_sweep(h);
+    h->stats.kernel_launches = launches;
+    h->prof_on = prof;
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    TN_CUDA_TRY(ce);
+    ce = cudaGraphInstantiate(&h->sweep_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    TN_CUDA_TRY(ce);
+    h->sweep_flops = h->sweep_bytes = 0.0;
+    for (auto& L : h->sweep.L) {
+      double f, b;
+      gemm_work(L.d, &f, &b);
+      h->sweep_flops += f;
+      h->sweep_bytes += b;
+    }
+  }
+  *use = true;
+  return TN_OK;
+}
+
 tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, double* res) {
   const int nmsg = 2 * (int)h->g.eu.size();
   // Messages are stored in FP32: once the residual is down at the rounding
@@ -842,22 +898,32 @@ tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, 
     st0 = ensure_mrt(h);
     if (st0) return st0;
   }
+  bool use_graph = false;
+  {
+    tn_status st0 = sweep_graph(h, &use_graph);
+    if (st0) return st0;
+  }
+  const int64_t per_sweep = (int64_t)h->sweep.L.size() + 1;
   for (it = 1; it <= max_iters; ++it) {
-    TN_CUDA_TRY(cudaMemsetAsync(h->res_bits, 0, sizeof(unsigned long long), h->stream));
-    tn_status st = run_plan(h, h->sweep, P_BP);
-    if (st) return st;
-    const int pi = prof_begin(h, P_NORM);
-    TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream,
-                                 h->mrt));
-    prof_end(h, pi, 0.0, 3.0 * 8.0 * h->chi * h->chi * nmsg);
-    h->stats.kernel_launches++;
-    unsigned long long bits = 0;
-    TN_CUDA_TRY(cudaMemcpyAsync(&bits, h->res_bits, sizeof(bits), cudaMemcpyDeviceToHost,
-                                h->stream));
+    if (use_graph) {
+      const int pi = prof_begin(h, P_BP);
+      TN_CUDA_TRY(cudaGraphLaunch(h->sweep_exec, h->stream));
+      prof_end(h, pi, h->sweep_flops, h->sweep_bytes);
+    } else {
+      tn_status st = enqueue_sweep(h);
+      if (st) return st;
+    }
+    h->stats.kernel_launches += per_sweep;
     TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const unsigned long long bits = h->h_status[0];
+    const int flags = (int)h->h_status[1];
     memcpy(&r, &bits, sizeof(r));
-    st = check_flags(h, "a BP sweep");
-    if (st) return st;
+    if (flags) {
+      TN_CUDA_TRY(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+      set_error(flags & 2 ? "a device-side wait gave up in a BP sweep"
+                          : "non-finite or zero-norm values detected in a BP sweep");
+      return flags & 2 ? TN_ETIMEOUT : TN_ENUMERIC;
+    }
     if (r < tol) break;
     hist.push_back(r);
     const size_t k = hist.size();
@@ -1074,7 +1140,7 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->work = (double*)dev_alloc(h, sizeof(double) * h->max_layer * solve_work_doubles(chi));
   h->solve_stats = (double*)dev_alloc(h, sizeof(double) * 4 * h->max_layer);
   h->res_bits = (unsigned long long*)dev_alloc(h, 64);
-  h->flags = (int*)dev_alloc(h, 64);
+  h->flags = h->res_bits ? reinterpret_cast<int*>(h->res_bits + 1) : nullptr;
   h->rho = (double*)dev_alloc(h, sizeof(double) * 8 * g.n);
   for (int d = 1; d <= 3; ++d) {
     h->n_by_deg[d] = (int)h->sites_by_deg[d].size();
@@ -1119,8 +1185,20 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
       return fail(TN_ECUDA);
     }
   }
-  cudaMemset(h->flags, 0, 64);
+  cudaMemset(h->res_bits, 0, 64);
+  if (cudaMallocHost(&h->h_status, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("pinned host allocation failed");
+    delete[] h->h_stats;
+    return fail(TN_ENOMEM);
+  }
   h->h_stats = new double[4 * std::max(1, h->max_layer)];
+  if ((use_tensor_cores(h) && tc_prepare() != cudaSuccess) || normalise_prepare(chi) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("setting kernel attributes failed");
+    delete[] h->h_stats;
+    return fail(TN_ECUDA);
+  }
   build_sweep_plan(h);
   h->gate_env.resize(nl);
   h->rebuild.resize(nl);
@@ -1154,6 +1232,8 @@ tn_status tn_destroy(tn_handle* h) {
   if (!h) return TN_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  if (h->h_status) cudaFreeHost(h->h_status);
   dev_free_all(h);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete[] h->h_stats;

@@ -333,6 +333,17 @@ cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site
   return cudaGetLastError();
 }
 
+static int g_norm_attr_bytes = 48 * 1024;
+
+cudaError_t normalise_prepare(int chi) {
+  const size_t sm = sizeof(float) * 2 * (size_t)chi * chi;
+  if (sm > 200 * 1024 || (int)sm <= g_norm_attr_bytes) return cudaSuccess;
+  cudaError_t e =
+      cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e == cudaSuccess) g_norm_attr_bytes = (int)sm;
+  return e;
+}
+
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
                              unsigned long long* res_bits, int* flags, cudaStream_t s, float* mrt) {
   if (n_msgs <= 0) return cudaSuccess;
@@ -343,9 +354,8 @@ cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
     if (e != cudaSuccess || !mrt) return e;
     return launch_realify(msg, 2 * (int64_t)chi * chi, mrt, n_msgs, chi, s);
   }
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(normalise_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  {
+    cudaError_t e = normalise_prepare(chi);
     if (e != cudaSuccess) return e;
   }
   normalise_kernel<<<n_msgs, 256, sm, s>>>(raw, msg, chi, res_bits, flags, mrt);

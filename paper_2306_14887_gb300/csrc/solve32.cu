@@ -32,7 +32,7 @@
 namespace tnbp {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChi = 64;

@@ -680,6 +680,20 @@ bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {
   return true;
 }
 
+// Kernel attributes, set once before any launch (and before any stream capture).
+cudaError_t tc_prepare() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes());
+  if (e != cudaSuccess) return e;
+  // two CTAs per SM: ask for the largest shared-memory carveout
+  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  done = true;
+  return cudaSuccess;
+}
+
 cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0 || d.n_outer <= 0 || d.n_inner <= 0) return cudaSuccess;
   int quad, splits;
@@ -699,15 +713,9 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
   t.k_per_split = (int)(((tiles + splits - 1) / splits) * kel);
   t.part = part;
   t.err = err;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes());
+  {
+    cudaError_t e = tc_prepare();
     if (e != cudaSuccess) return e;
-    // two CTAs per SM: ask for the largest shared-memory carveout
-    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   dim3 grid((t.nr + t.tn - 1) / t.tn, (t.mr + kTM - 1) / kTM, d.n_outer * d.n_inner * splits);
   tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(), st>>>(d, t);
