@@ -96,7 +96,19 @@ typedef struct {
                            <= 0 selects the precision's default */
   uint64_t seed;        /* reserved (the method draws no random numbers) */
   int32_t solve;        /* truncation solve: TN_SOLVE_AUTO, TN_SOLVE_FP64 or TN_SOLVE_SHARED */
+  int32_t kernels;      /* contraction kernels: TN_KERNELS_AUTO or TN_KERNELS_TILE */
 } tn_config;
+
+/* Contraction kernels of the tensor-core modes.
+ * TN_KERNELS_AUTO: with TN_TF32 and chi = 32 or 64, the mode products (one leg
+ *   of a site tensor times a chi x chi matrix: the BP sweep's first two
+ *   contractions per chain, the gate environments and rebuilds) run in the
+ *   persistent TMA-fed streaming kernel; every other contraction, and every
+ *   contraction of the other modes, in the generic tile kernel.
+ * TN_KERNELS_TILE: the generic tile kernel for every contraction.
+ * The two give the same sums in different rounding orders. */
+#define TN_KERNELS_AUTO 0
+#define TN_KERNELS_TILE 1
 
 /* Truncation solve variants.
  * TN_SOLVE_FP64: Hermitian Jacobi eigen-solves in FP64 on global-memory
@@ -130,6 +142,7 @@ typedef struct {
   double discarded_max;      /* largest discarded weight sum(sigma^2 dropped)/sum(sigma^2) */
   double discarded_sum;      /* summed over all gates of the call */
   int64_t kernel_launches;   /* device kernels launched by the call */
+  int64_t tma_launches;      /* of which launches of the TMA-fed streaming kernel */
 } tn_stats;
 
 /*

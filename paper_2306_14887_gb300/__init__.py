@@ -22,6 +22,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ENOTCONVERGED",
           -8: "TN_EUNSUPPORTED"}
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
 SOLVES = {"auto": 0, "fp64": 1, "shared": 2}
+KERNELS = {"auto": 0, "tile": 1}
 
 #: every symbol include/tnbp.h declares
 EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dagger",
@@ -48,7 +49,7 @@ class tn_graph(C.Structure):
 class tn_config(C.Structure):
     _fields_ = [("chi", C.c_int32), ("prec", C.c_int32), ("bp_tol", C.c_double),
                 ("bp_max_iters", C.c_int32), ("svd_cutoff", C.c_double), ("seed", C.c_uint64),
-                ("solve", C.c_int32)]
+                ("solve", C.c_int32), ("kernels", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -63,7 +64,7 @@ class tn_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int32), ("bp_iters_last", C.c_int32),
                 ("bp_iters_total", C.c_int32), ("bp_residual_last", C.c_double),
                 ("discarded_max", C.c_double), ("discarded_sum", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("tma_launches", C.c_int64)]
 
 
 class tn_profile(C.Structure):
@@ -189,9 +190,10 @@ def _graph_struct(n, edges, colours):
     return g, keep
 
 
-def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve="auto"):
+def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve="auto", kernels="auto"):
     c = tn_config()
     c.solve = SOLVES[solve] if isinstance(solve, str) else int(solve)
+    c.kernels = KERNELS[kernels] if isinstance(kernels, str) else int(kernels)
     c.chi = int(chi)
     c.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     c.bp_tol = float(bp_tol)
@@ -214,7 +216,7 @@ class TNState:
 
     def __init__(self, n, edges, colours=None, chi=8, prec="fp32", bp_tol=1e-10,
                  bp_max_iters=1000, svd_cutoff=0.0, stream=None, torch_allocator=True,
-                 solve="auto"):
+                 solve="auto", kernels="auto"):
         import torch
         self._torch = torch
         L = lib()
@@ -222,7 +224,7 @@ class TNState:
         self.edges = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
         self.chi = int(chi)
         g, self._keep = _graph_struct(n, edges, colours)
-        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve)
+        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve, kernels)
         if stream is None:
             # a stream of its own: the library captures its BP sweep as a CUDA
             # graph, which the legacy default stream does not allow

@@ -83,7 +83,21 @@ cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s);
 // scratch for K-split partial products (tc_plan gives the size); err: bit 1 is
 // set when a device-side wait gave up.
 bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats);
-cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t s);
+cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t s,
+                            int* n_kernels = nullptr);
+// Persistent TMA-fed kernel for mode products (tc_stream.cu): one A and one B
+// tensor map per batch entry, encoded on the host when a plan is uploaded.
+struct TcStreamPlan {
+  const void* maps = nullptr;  // device CUtensorMap[2 * n_outer]
+  int n_outer = 0, rank = 0, lev0 = 1, lev1 = 1;
+};
+// Fills host_maps (tc_stream_map_bytes(n_outer) bytes, 64-byte aligned) and
+// the plan's shape fields; false when the descriptor is not eligible.
+bool tc_stream_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
+                      void* host_maps, TcStreamPlan* p);
+size_t tc_stream_map_bytes(int n_outer);
+cudaError_t tc_stream_prepare();
+cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err, cudaStream_t s);
 // Kernel attributes set once, before any launch or stream capture.
 cudaError_t tc_prepare();
 cudaError_t normalise_prepare(int chi);

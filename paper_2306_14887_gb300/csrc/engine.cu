@@ -46,6 +46,7 @@ struct HostLaunch {
   GemmDesc d;
   std::vector<const float*> A, B;
   std::vector<float*> C;
+  TcStreamPlan sp;  // maps set: the launch runs in the streaming kernel
 };
 
 struct Plan {
@@ -120,6 +121,7 @@ struct tn_handle {
   // contraction launches, normalisation, read-back of the status words)
   cudaGraphExec_t sweep_exec = nullptr;
   double sweep_flops = 0.0, sweep_bytes = 0.0;
+  int64_t sweep_kernels = 0, sweep_tma = 0;  // launches inside the captured sweep
   unsigned long long* h_status = nullptr;  // pinned: [residual bits, flags]
 
   // per-kernel-class timing with CUDA events on the handle's stream
@@ -284,6 +286,39 @@ tn_status upload_plans(tn_handle* h) {
   }
   TN_CUDA_TRY(cudaMemcpyAsync(arena, host.data(), bytes, cudaMemcpyHostToDevice, h->stream));
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  // tensor maps of the mode products that the streaming kernel takes
+  if (h->cfg.prec == TN_TF32 && h->cfg.kernels == TN_KERNELS_AUTO) {
+    size_t mbytes = 0;
+    for (Plan* p : plans)
+      for (auto& L : p->L) mbytes += tc_stream_map_bytes((int)L.A.size());
+    std::vector<unsigned char> hm(mbytes + 64);
+    unsigned char* base =
+        (unsigned char*)(((uintptr_t)hm.data() + 63) & ~uintptr_t(63));
+    std::vector<HostLaunch*> users;
+    std::vector<size_t> offs;
+    size_t mpos = 0;
+    for (Plan* p : plans)
+      for (auto& L : p->L) {
+        TcStreamPlan sp;
+        if (tc_stream_encode(L.d, L.A.data(), L.B.data(), (int)L.A.size(), base + mpos, &sp)) {
+          L.sp = sp;
+          users.push_back(&L);
+          offs.push_back(mpos);
+          mpos += tc_stream_map_bytes((int)L.A.size());
+        }
+      }
+    if (mpos > 0) {
+      void* dm = dev_alloc(h, mpos);
+      if (!dm) {
+        set_error("device allocation of the tensor maps failed");
+        return TN_ENOMEM;
+      }
+      TN_CUDA_TRY(cudaMemcpyAsync(dm, base, mpos, cudaMemcpyHostToDevice, h->stream));
+      TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+      for (size_t i = 0; i < users.size(); ++i) users[i]->sp.maps = (unsigned char*)dm + offs[i];
+      TN_CUDA_TRY(tc_stream_prepare());
+    }
+  }
   return TN_OK;
 }
 
@@ -359,8 +394,12 @@ bool use_tensor_cores(const tn_handle* h) {
 tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
   for (auto& L : P.L) {
     const int pi = prof_begin(h, cls);
-    if (use_tensor_cores(h)) {
-      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, h->stream));
+    int nk = 1;
+    if (L.sp.maps) {
+      TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, h->stream));
+      h->stats.tma_launches++;
+    } else if (use_tensor_cores(h)) {
+      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, h->stream, &nk));
     } else {
       TN_CUDA_TRY(launch_cgemm(L.d, h->stream));
     }
@@ -369,7 +408,7 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
       gemm_work(L.d, &f, &b);
       prof_end(h, pi, f, b);
     }
-    h->stats.kernel_launches++;
+    h->stats.kernel_launches += nk;
   }
   return TN_OK;
 }
@@ -842,6 +881,7 @@ tn_status enqueue_sweep(tn_handle* h) {
   TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream,
                                h->mrt));
   prof_end(h, pi, 0.0, 3.0 * 8.0 * h->chi * h->chi * nmsg);
+  h->stats.kernel_launches++;
   TN_CUDA_TRY(cudaMemcpyAsync(h->h_status, h->res_bits, 2 * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, h->stream));
   return TN_OK;
@@ -857,9 +897,13 @@ tn_status sweep_graph(tn_handle* h, bool* use) {
     const bool prof = h->prof_on;
     h->prof_on = false;
     TN_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    const int64_t launches = h->stats.kernel_launches;
+    const int64_t launches = h->stats.kernel_launches, tma = h->stats.tma_launches;
     tn_status st = enqueue_sweep(h);
+    // the captured sweep's launch counts, charged once per graph launch
+    h->sweep_kernels = h->stats.kernel_launches - launches;
+    h->sweep_tma = h->stats.tma_launches - tma;
     h->stats.kernel_launches = launches;
+    h->stats.tma_launches = tma;
     h->prof_on = prof;
     cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
     if (st) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -903,7 +947,7 @@ tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, 
     tn_status st0 = sweep_graph(h, &use_graph);
     if (st0) return st0;
   }
-  const int64_t per_sweep = (int64_t)h->sweep.L.size() + 1;
+
   for (it = 1; it <= max_iters; ++it) {
     if (use_graph) {
       const int pi = prof_begin(h, P_BP);
@@ -913,7 +957,10 @@ tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, 
       tn_status st = enqueue_sweep(h);
       if (st) return st;
     }
-    h->stats.kernel_launches += per_sweep;
+    if (use_graph) {
+      h->stats.kernel_launches += h->sweep_kernels;
+      h->stats.tma_launches += h->sweep_tma;
+    }
     TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
     const unsigned long long bits = h->h_status[0];
     const int flags = (int)h->h_status[1];
@@ -1074,6 +1121,10 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64) {
     set_error("unknown truncation solve");
+    return TN_EINVAL;
+  }
+  if (cfg->kernels != TN_KERNELS_AUTO && cfg->kernels != TN_KERNELS_TILE) {
+    set_error("unknown kernel selection");
     return TN_EINVAL;
   }
   if (!(cfg->bp_tol > 0) || cfg->bp_max_iters < 1) {

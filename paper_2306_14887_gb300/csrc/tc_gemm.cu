@@ -29,10 +29,13 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 #include "tnbp.h"
 
 namespace tnbp {
 namespace {
+
+using namespace tc;
 
 constexpr int kTM = 128;          // tile rows (MMA M)
 constexpr int kTN = 128;          // max tile columns (MMA N)
@@ -40,7 +43,6 @@ constexpr int kRowBytes = 128;    // one K tile = one swizzled 128-byte row per 
 constexpr int kStages = 3;
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 128;
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 constexpr int kBatch = 8;                        // 16-byte loads in flight per producer thread
 
 struct TcSmem {
@@ -49,131 +51,6 @@ struct TcSmem {
   static constexpr int kBarOff = kStages * (kA + kB);
   static constexpr int kBytes = kBarOff + 128;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for the phase of the given parity to complete.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > kWaitCycles) {
-      atomicOr(err, 2);
-      return false;
-    }
-    __nanosleep(40);
-  }
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// 16-byte asynchronous copy global -> shared (zero fill when !valid).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-               "r"(valid ? 16 : 0)
-               : "memory");
-}
-// Arrive on the mbarrier once this thread's prior cp.async copies have landed.
-__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
-  d |= (uint64_t)1 << 16;                           // leading byte offset (unused)
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
-  d |= (uint64_t)1 << 46;                           // version
-  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulate, A/B format fmt (1 BF16, 2 TF32),
-// both K-major, N and M encoded.
-__host__ __device__ constexpr uint32_t make_idesc(int fmt, int M, int N) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_issue(int bf16, uint32_t d_tmem, uint64_t a, uint64_t b,
-                                          uint32_t idesc, uint32_t acc) {
-  if (bf16) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 __device__ __forceinline__ int64_t koff(int k, int K2, int64_t s1, int64_t s2) {
   const int k1 = k / K2;
@@ -694,7 +571,9 @@ cudaError_t tc_prepare() {
   return cudaSuccess;
 }
 
-cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t st) {
+cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t st,
+                            int* n_kernels) {
+  if (n_kernels) *n_kernels = 0;
   if (d.M <= 0 || d.N <= 0 || d.n_outer <= 0 || d.n_inner <= 0) return cudaSuccess;
   int quad, splits;
   size_t pf;
@@ -719,6 +598,7 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
   }
   dim3 grid((t.nr + t.tn - 1) / t.tn, (t.mr + kTM - 1) / kTM, d.n_outer * d.n_inner * splits);
   tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(), st>>>(d, t);
+  if (n_kernels) *n_kernels = splits > 1 ? 2 : 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   dim3 rg((d.M * d.N + 255) / 256, d.n_outer * d.n_inner);

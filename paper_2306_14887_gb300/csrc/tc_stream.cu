@@ -1,0 +1,457 @@
+// Persistent TMA-fed tensor-core kernel for the mode products of the BP sweep
+// and the gate (Eq. MessageTensorSelfConsistency contracted leg by leg):
+//   Y[m][(t, n)] = sum_(s, k) A_s[m][k] Bt[(t, n)][(s, k)],
+// A a site-shaped planar complex tensor whose rows m (all legs but the
+// contracted one, and p) are streamed once, Bt the realified transposed
+// chi x chi message (a real [2 chi][2 chi] matrix, the same for every row of
+// one site).  With chi = 64 one site is 64 tiles of 128 rows; the operand
+// streams at HBM rate while the tensor core does 4.2 MFLOP per 128 KB of
+// traffic, so the kernel is bound by HBM, not by the tensor pipe.
+//
+// One CTA per SM walks a contiguous range of (site, row tile) pairs:
+//   warp 0 (one thread)  TMA producer: the site's Bt once per site (4 chunks
+//                        of [2 chi rows][32 floats], 128-byte swizzle), then
+//                        per tile the 2 chi / 32 K chunks of A, [128 rows][32
+//                        floats] each, into an 8-slot ring (full / empty
+//                        mbarriers, transaction counts);
+//   warp 1 (one thread)  tcgen05.mma (M = 128, N = 2 chi, K = 8 TF32) into one
+//                        of two TMEM accumulators, commits release the ring
+//                        slot, the accumulator and, at a site change, Bt;
+//   warps 2..5           epilogue: tcgen05.ld of their 32-lane quadrant,
+//                        coalesced stores (consecutive rows are consecutive
+//                        addresses in every output layout the engine builds),
+//                        then release the accumulator, so the store of tile i
+//                        overlaps the loads and MMAs of tile i + 1.
+// The A rows are addressed by a TMA tensor map over (k, up to three row
+// levels, plane); the engine encodes one map per site when it builds a plan.
+// Every mbarrier wait is bounded (about one second): on expiry the kernel sets
+// bit 1 of *err, stops issuing, waits (bounded) for the copies and MMAs it has
+// in flight and frees its tensor memory.
+#include <cuda.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "tc_common.cuh"
+#include "tnbp.h"
+
+namespace tnbp {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 192;
+constexpr int kSlots = 8;                 // A ring: 8 x 16 KB
+constexpr int kChunk = 128 * 128;         // one [128 rows][128 bytes] chunk
+constexpr int kBBytes = 4 * kChunk;       // Bt: up to 4 chunks of [128 rows][128 bytes]
+constexpr int kBarOff = kBBytes + kSlots * kChunk;
+constexpr int kSmemBytes = kBarOff + 256 + 1024;  // barriers + alignment slack
+
+struct StreamArgs {
+  const CUtensorMap* maps;  // [2 * n_outer]: A maps, then Bt maps
+  int n_outer;
+  int tiles_per_entry;      // M / 128
+  int kc;                   // K chunks of 32 floats: 2 chi / 32
+  int nr;                   // real N: 2 chi
+  int chi;
+  int rank;                 // A map rank: 2 + number of row levels
+  int lev0, lev1;           // sizes of the two innermost row levels (for coordinates)
+  int* err;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, StreamArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + kBBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  uint64_t* empty = full + kSlots;
+  uint64_t* bfull = empty + kSlots;
+  uint64_t* bempty = bfull + 1;
+  uint64_t* tfull = bempty + 1;   // [2]
+  uint64_t* tempty = tfull + 2;   // [2]
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int total = a.n_outer * a.tiles_per_entry;
+  const int t_beg = (int)((int64_t)blockIdx.x * total / gridDim.x);
+  const int t_end = (int)((int64_t)(blockIdx.x + 1) * total / gridDim.x);
+  const uint32_t tmem_cols = 2 * a.nr;  // two accumulators of nr columns (128 or 256)
+
+  if (tid == 0) {
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(bempty, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const CUtensorMap* amaps = a.maps;
+  const CUtensorMap* bmaps = a.maps + a.n_outer;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- producer
+    if (lane == 0) {
+      int it = 0, cur = -1, bl = 0;
+      int issued[kSlots];
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) issued[s] = 0;
+      const uint32_t bbytes = (uint32_t)(a.kc * a.nr * 128);
+      for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile) {
+        const int e = tile / a.tiles_per_entry;
+        const int mt = tile - e * a.tiles_per_entry;
+        if (e != cur) {
+          if (cur >= 0 && !mbar_wait(bempty, (bl - 1) & 1, a.err)) { *abort_flag = 1; break; }
+          mbar_expect_tx(bfull, bbytes);
+          for (int c = 0; c < a.kc; ++c)
+            tma_load_2d(smem_u32(sB + c * a.nr * 128), bmaps + e, c * 32, 0, bfull);
+          ++bl;
+          cur = e;
+        }
+        // row coordinates of the tile's first row in the map's row levels
+        int r = mt * 128;
+        const int r0 = r % a.lev0;
+        r /= a.lev0;
+        const int r1 = r % a.lev1;
+        const int r2 = r / a.lev1;
+        for (int c = 0; c < a.kc; ++c, ++it) {
+          const int slot = it % kSlots;
+          if (!mbar_wait(&empty[slot], ((it / kSlots) & 1) ^ 1, a.err)) { *abort_flag = 1; break; }
+          mbar_expect_tx(&full[slot], (uint32_t)kChunk);
+          const int kr = c * 32, plane = kr / a.chi, k = kr - plane * a.chi;
+          const uint32_t dst = smem_u32(sA + slot * kChunk);
+          if (a.rank == 3) tma_load_3d(dst, amaps + e, k, r0, plane, &full[slot]);
+          else if (a.rank == 4) tma_load_4d(dst, amaps + e, k, r0, r1, plane, &full[slot]);
+          else tma_load_5d(dst, amaps + e, k, r0, r1, r2, plane, &full[slot]);
+          ++issued[slot];
+        }
+      }
+      // before the CTA exits: every copy issued has landed (immediate on the
+      // normal path, where the consumer already waited for each of them)
+      for (int s = 0; s < kSlots; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (issued[s] - 1) & 1, a.err);
+      if (bl > 0) mbar_wait(bfull, (bl - 1) & 1, a.err);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(2, 128, a.nr);
+      int it = 0, cur = -1, bl = 0, i = 0;
+      for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile, ++i) {
+        const int e = tile / a.tiles_per_entry;
+        if (e != cur) {
+          if (cur >= 0) mma_commit(bempty);  // arrives once the MMAs reading Bt are done
+          if (!mbar_wait(bfull, bl & 1, a.err)) { *abort_flag = 1; break; }
+          ++bl;
+          cur = e;
+        }
+        const int acc = i & 1;
+        if (!mbar_wait(&tempty[acc], ((i >> 1) & 1) ^ 1, a.err)) { *abort_flag = 1; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(acc * a.nr);
+        bool ok = true;
+        for (int c = 0; c < a.kc; ++c, ++it) {
+          const int slot = it % kSlots;
+          if (!mbar_wait(&full[slot], (it / kSlots) & 1, a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + slot * kChunk);
+          const uint32_t b0 = smem_u32(sB + c * a.nr * 128);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            mma_issue(0, d_tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+                      (c > 0 || ks > 0) ? 1u : 0u);
+          mma_commit(&empty[slot]);
+        }
+        if (!ok) { *abort_flag = 1; break; }
+        mma_commit(&tfull[acc]);
+      }
+      // all MMAs issued by this thread complete before TMEM is freed
+      mma_commit(done);
+      mbar_wait(done, 0, a.err);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row = q * 32 + lane;
+    int i = 0;
+    for (int tile = t_beg; tile < t_end; ++tile, ++i) {
+      if (*abort_flag) break;
+      const int e = tile / a.tiles_per_entry;
+      const int mt = tile - e * a.tiles_per_entry;
+      const int acc = i & 1;
+      const bool ok = mbar_wait(&tfull[acc], (i >> 1) & 1, a.err);
+      if (!ok) { *abort_flag = 1; break; }
+      tc_fence_after();
+      __syncwarp();
+      const int m = mt * 128 + row;
+      float* C = d.C[e] + ROW_C(d, m);
+      for (int c0 = 0; c0 < a.nr; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * a.nr + c0), v);
+        const int t = c0 >= a.chi;
+        float* Cc = C + (t ? d.plane_c : 0) + (int64_t)(c0 - t * a.chi) * d.c_n;
+        if (d.c_n == 1) {
+          // columns contiguous in the output: 16-byte stores along the row
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4*>(Cc + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+          // rows contiguous: lane-consecutive addresses, one 128-byte store per column
+#pragma unroll
+          for (int j = 0; j < 32; ++j) Cc[(int64_t)j * d.c_n] = v[j];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Row levels of the descriptor's A operand, innermost first, adjacent levels
+// merged where they are contiguous, then boxed into 128-row tiles.
+struct Levels {
+  int n = 0;
+  int64_t size[3], stride[3];
+  int box[3];
+};
+
+bool row_levels(const GemmDesc& d, Levels* L) {
+  int64_t sz[3], st[3];
+  int n = 0;
+  if (d.M3 > 1) {
+    if (d.M % (d.M2 * d.M3)) return false;
+    sz[0] = d.M3; st[0] = d.a_m3; sz[1] = d.M2; st[1] = d.a_m2; sz[2] = d.M / (d.M2 * d.M3);
+    st[2] = d.a_m; n = 3;
+  } else if (d.M2 > 1) {
+    if (d.M % d.M2) return false;
+    sz[0] = d.M2; st[0] = d.a_m2; sz[1] = d.M / d.M2; st[1] = d.a_m; n = 2;
+  } else {
+    sz[0] = d.M; st[0] = d.a_m; n = 1;
+  }
+  // drop unit levels, merge contiguous neighbours
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    if (sz[i] == 1) continue;
+    if (m > 0 && st[i] == L->size[m - 1] * L->stride[m - 1]) {
+      L->size[m - 1] *= sz[i];
+      continue;
+    }
+    L->size[m] = sz[i];
+    L->stride[m] = st[i];
+    ++m;
+  }
+  if (m == 0) { L->size[0] = 1; L->stride[0] = d.a_m; m = 1; }
+  L->n = m;
+  int64_t rem = 128;
+  for (int i = 0; i < m; ++i) {
+    if (rem == 1) { L->box[i] = 1; continue; }
+    if (L->size[i] >= rem) {
+      if (L->size[i] % rem) return false;
+      L->box[i] = (int)rem;
+      rem = 1;
+    } else {
+      if (rem % L->size[i]) return false;
+      L->box[i] = (int)L->size[i];
+      rem /= L->size[i];
+    }
+  }
+  return rem == 1;
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+bool tc_stream_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
+                      void* host_maps, TcStreamPlan* p) {
+  const int chi = d.N;
+  if (d.prec != TN_TF32 || !d.b_pre || d.K1 != 1 || d.K2 != chi || d.a_k2 != 1 || d.conj_a ||
+      d.accumulate || d.n_inner != 1 || (chi != 32 && chi != 64) || d.M % 128 != 0 ||
+      n_outer < 1)
+    return false;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  Levels L;
+  if (!row_levels(d, &L)) return false;
+  const int rank = L.n + 2;
+  if (rank > 5) return false;
+  for (int i = 0; i < L.n; ++i)
+    if ((L.stride[i] * 4) % 16 || L.stride[i] * 4 >= (int64_t(1) << 40)) return false;
+  if ((d.plane_a * 4) % 16) return false;
+  if (d.c_n == 1 && (d.c_m % 4 || (d.M2 > 1 && d.c_m2 % 4) || (d.M3 > 1 && d.c_m3 % 4) ||
+                     d.plane_c % 4))
+    return false;
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host_maps);
+  for (int e = 0; e < n_outer; ++e) {
+    if ((reinterpret_cast<uintptr_t>(A[e]) & 15) || (reinterpret_cast<uintptr_t>(B[e]) & 15))
+      return false;
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    dims[0] = (cuuint64_t)chi;
+    box[0] = 32;
+    for (int i = 0; i < L.n; ++i) {
+      dims[1 + i] = (cuuint64_t)L.size[i];
+      strides[i] = (cuuint64_t)(L.stride[i] * 4);
+      box[1 + i] = (cuuint32_t)L.box[i];
+    }
+    dims[rank - 1] = 2;
+    strides[rank - 2] = (cuuint64_t)(d.plane_a * 4);
+    box[rank - 1] = 1;
+    if (enc(&maps[e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+            const_cast<float*>(A[e]), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    // Bt: real [2 chi][2 chi] row-major
+    cuuint64_t bd[2] = {(cuuint64_t)(2 * chi), (cuuint64_t)(2 * chi)};
+    cuuint64_t bs[1] = {(cuuint64_t)(2 * chi * 4)};
+    cuuint32_t bb[2] = {32, (cuuint32_t)(2 * chi)};
+    if (enc(&maps[n_outer + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(B[e]), bd,
+            bs, bb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  p->rank = rank;
+  p->lev0 = (int)(L.n > 0 ? L.size[0] : 1);
+  p->lev1 = (int)(L.n > 1 ? L.size[1] : 1);
+  if (rank == 3) p->lev0 = (int)L.size[0];
+  p->n_outer = n_outer;
+  return true;
+}
+
+size_t tc_stream_map_bytes(int n_outer) { return (size_t)2 * n_outer * sizeof(CUtensorMap); }
+
+cudaError_t tc_stream_prepare() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(tc_stream_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  done = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err, cudaStream_t st) {
+  cudaError_t e = tc_stream_prepare();
+  if (e != cudaSuccess) return e;
+  StreamArgs a;
+  a.maps = reinterpret_cast<const CUtensorMap*>(p.maps);
+  a.n_outer = p.n_outer;
+  a.tiles_per_entry = d.M / 128;
+  a.chi = d.N;
+  a.nr = 2 * d.N;
+  a.kc = 2 * d.N / 32;
+  a.rank = p.rank;
+  a.lev0 = p.lev0;
+  a.lev1 = p.lev1;
+  a.err = err;
+  const int total = a.n_outer * a.tiles_per_entry;
+  const int grid = total < g_num_sms ? total : g_num_sms;
+  tc_stream_kernel<<<grid, kThreads, kSmemBytes, st>>>(d, a);
+  return cudaGetLastError();
+}
+
+}  // namespace tnbp

@@ -83,3 +83,56 @@ def test_tensor_core_evolution_within_stated_bound(tnlib, prec, graph, chi, step
     s.apply_floquet(theta, steps)
     assert np.abs(s.expect_z_all() - o.all_z()).max() < Z_TOL[prec]
     s.close()
+
+
+# The persistent TMA-fed streaming kernel takes the mode products at chi = 32
+# and 64 in TF32 (kernels="auto"); kernels="tile" keeps every contraction in
+# the generic tile kernel.  Same TF32 operands, different accumulation order.
+@pytest.mark.parametrize("chi", [32, 64])
+def test_streaming_sweep_matches_oracle_127(tnlib, chi):
+    g = OG.eagle127()
+    tensors, msgs = random_state([g.degree(v) for v in range(g.n)], g.edges, chi, seed=5)
+    got = {}
+    for kern in ("auto", "tile"):
+        s = tnlib.TNState(g.n, g.edges, g.colours, chi=chi, prec="tf32", kernels=kern)
+        for v in range(g.n):
+            s.set_site(v, tensors[v])
+        for (src, e), m in msgs.items():
+            s.set_message(e, src, m)
+        s.bp_converge(tol=1e30, max_iters=1)
+        st = s.stats()
+        # every degree-3 chain's two mode products: 6 streaming launches per sweep
+        assert (st["tma_launches"] >= 6) if kern == "auto" else (st["tma_launches"] == 0)
+        got[kern] = {k: s.get_message(k[1], k[0]) for k in msgs}
+        s.close()
+    o = OB.BPState(g, chi)
+    o.T = [t.astype(complex) for t in tensors]
+    o.M = {k: m.astype(complex) for k, m in msgs.items()}
+    o.bp_sweep()
+    for kern in ("auto", "tile"):
+        err = max(np.abs(got[kern][k] - o.M[k]).max() for k in o.M)
+        assert err < SWEEP_TOL["tf32"], (kern, err)
+    # the two kernels see the same rounded operands
+    diff = max(np.abs(got["auto"][k] - got["tile"][k]).max() for k in o.M)
+    assert diff < 1e-4
+
+
+def test_streaming_evolution_chi32_127_matches_oracle(tnlib):
+    g = OG.eagle127()
+    o = OB.run(g, 32, 0.6, 4)
+    s = tnlib.TNState(g.n, g.edges, g.colours, chi=32, prec="tf32", kernels="auto")
+    s.apply_floquet(0.6, 4)
+    assert s.stats()["tma_launches"] > 0
+    assert np.abs(s.expect_z_all() - o.all_z()).max() < Z_TOL["tf32"]
+    s.close()
+
+
+def test_streaming_and_tile_kernels_agree_chi64_saturated(tnlib):
+    g = OG.eagle127()
+    z = {}
+    for kern in ("auto", "tile"):
+        s = tnlib.TNState(g.n, g.edges, g.colours, chi=64, prec="tf32", kernels=kern)
+        s.apply_floquet(0.9425, 8)
+        z[kern] = s.expect_z_all()
+        s.close()
+    assert np.abs(z["auto"] - z["tile"]).max() < Z_TOL["tf32"]
