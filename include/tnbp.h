@@ -97,6 +97,10 @@ typedef struct {
   uint64_t seed;        /* reserved (the method draws no random numbers) */
   int32_t solve;        /* truncation solve: TN_SOLVE_AUTO, TN_SOLVE_FP64 or TN_SOLVE_SHARED */
   int32_t kernels;      /* contraction kernels: TN_KERNELS_AUTO or TN_KERNELS_TILE */
+  double solve_tol;     /* shared solve: Jacobi stops when every pair of rows of the bond
+                           matrix has |<x_p, x_q>| <= solve_tol ||x_p|| ||x_q||; <= 0 selects
+                           the precision's default (2e-6 for TN_FP32, 1e-4 for TN_TF32,
+                           1e-3 for TN_BF16: about the relative rounding of the Gram inputs) */
 } tn_config;
 
 /* Contraction kernels of the tensor-core modes.
@@ -143,6 +147,8 @@ typedef struct {
   double discarded_sum;      /* summed over all gates of the call */
   int64_t kernel_launches;   /* device kernels launched by the call */
   int64_t tma_launches;      /* of which launches of the TMA-fed streaming kernel */
+  int64_t solve_edges;       /* truncation solves (gate edges) of the call */
+  int64_t solve_sweeps;      /* Jacobi rotation sweeps summed over those solves */
 } tn_stats;
 
 /*

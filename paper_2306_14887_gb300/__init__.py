@@ -49,7 +49,8 @@ class tn_graph(C.Structure):
 class tn_config(C.Structure):
     _fields_ = [("chi", C.c_int32), ("prec", C.c_int32), ("bp_tol", C.c_double),
                 ("bp_max_iters", C.c_int32), ("svd_cutoff", C.c_double), ("seed", C.c_uint64),
-                ("solve", C.c_int32), ("kernels", C.c_int32)]
+                ("solve", C.c_int32), ("kernels", C.c_int32),
+                ("solve_tol", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -64,7 +65,8 @@ class tn_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int32), ("bp_iters_last", C.c_int32),
                 ("bp_iters_total", C.c_int32), ("bp_residual_last", C.c_double),
                 ("discarded_max", C.c_double), ("discarded_sum", C.c_double),
-                ("kernel_launches", C.c_int64), ("tma_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("tma_launches", C.c_int64),
+                ("solve_edges", C.c_int64), ("solve_sweeps", C.c_int64)]
 
 
 class tn_profile(C.Structure):
@@ -190,8 +192,10 @@ def _graph_struct(n, edges, colours):
     return g, keep
 
 
-def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve="auto", kernels="auto"):
+def _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve="auto", kernels="auto",
+            solve_tol=0.0):
     c = tn_config()
+    c.solve_tol = float(solve_tol)
     c.solve = SOLVES[solve] if isinstance(solve, str) else int(solve)
     c.kernels = KERNELS[kernels] if isinstance(kernels, str) else int(kernels)
     c.chi = int(chi)
@@ -216,7 +220,7 @@ class TNState:
 
     def __init__(self, n, edges, colours=None, chi=8, prec="fp32", bp_tol=1e-10,
                  bp_max_iters=1000, svd_cutoff=0.0, stream=None, torch_allocator=True,
-                 solve="auto", kernels="auto"):
+                 solve="auto", kernels="auto", solve_tol=0.0):
         import torch
         self._torch = torch
         L = lib()
@@ -224,7 +228,7 @@ class TNState:
         self.edges = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
         self.chi = int(chi)
         g, self._keep = _graph_struct(n, edges, colours)
-        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve, kernels)
+        cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve, kernels, solve_tol)
         if stream is None:
             # a stream of its own: the library captures its BP sweep as a CUDA
             # graph, which the legacy default stream does not allow

@@ -153,6 +153,8 @@ struct SolveArgs {
   double* stats;            // per edge: [discarded weight, kept, sigma_1, min_gap]
   int* flags;
   int max_sweeps;
+  float orth_tol = 2e-6f;   // shared solve: pairs with |<x_p, x_q>| below
+                            // orth_tol ||x_p|| ||x_q|| count as orthogonal
 };
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s);
 size_t solve_work_doubles(int chi);

@@ -788,6 +788,15 @@ void rx_matrix(double theta, double u[8]) {
   u[4] = 0; u[5] = -s; u[6] = c; u[7] = 0;
 }
 
+// Orthogonality tolerance of the shared solve's Jacobi: about the relative
+// rounding of its Gram inputs, which the contraction precision sets.
+double solve_tol(const tn_handle* h) {
+  if (h->cfg.solve_tol > 0) return h->cfg.solve_tol;
+  if (h->cfg.prec == TN_TF32) return 1e-4;
+  if (h->cfg.prec == TN_BF16) return 1e-3;
+  return 2e-6;
+}
+
 double default_svd_cut(const tn_handle* h) {
   if (h->cfg.svd_cutoff > 0) return h->cfg.svd_cutoff;
   return h->cfg.prec == TN_FP32 || h->cfg.prec == TN_TF32X3 || h->cfg.prec == TN_BF16X3 ? 1e-6
@@ -836,6 +845,7 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
     const int pi = prof_begin(h, P_SOLVE);
     if (use_shared_solve(h)) {
       a.max_sweeps = 20;
+      a.orth_tol = (float)solve_tol(h);
       TN_CUDA_TRY(launch_solve32(a, h->stream));
     } else {
       TN_CUDA_TRY(launch_solve(a, h->stream));
@@ -864,6 +874,8 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
   for (int i = 0; i < ne; ++i) {
     const double dw = h->h_stats[4 * i];
+    h->stats.solve_edges++;
+    h->stats.solve_sweeps += (int64_t)h->h_stats[4 * i + 3];
     h->stats.discarded_sum += dw;
     h->stats.discarded_max = std::max(h->stats.discarded_max, dw);
   }
@@ -1121,6 +1133,10 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64) {
     set_error("unknown truncation solve");
+    return TN_EINVAL;
+  }
+  if (!(cfg->solve_tol < 0.1)) {
+    set_error("solve_tol must be below 0.1");
     return TN_EINVAL;
   }
   if (cfg->kernels != TN_KERNELS_AUTO && cfg->kernels != TN_KERNELS_TILE) {

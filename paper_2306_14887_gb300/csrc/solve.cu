@@ -54,15 +54,16 @@ constexpr int kMaxN = 512;  // 2 * chi for chi <= 256
 // diagonal ends up holding the eigenvalues).  V receives the eigenvectors as
 // columns.  The n/2 disjoint rotations of one round-robin round are applied
 // together: all column updates (A J, V J), then all row updates (J^H A).
-__device__ void jacobi_eig(cd* A, cd* V, int n, int max_sweeps, double* sh,
-                           double* rc, double* rs, cd* rph) {
+__device__ int jacobi_eig(cd* A, cd* V, int n, int max_sweeps, double* sh,
+                          double* rc, double* rs, cd* rph) {
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
     V[idx] = {i == j ? 1.0 : 0.0, 0.0};
   }
   __syncthreads();
   const int half = n / 2;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
     double off = 0.0, dg = 0.0;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int i = idx / n, j = idx - i * n;
@@ -123,6 +124,7 @@ __device__ void jacobi_eig(cd* A, cd* V, int n, int max_sweeps, double* sh,
       __syncthreads();
     }
   }
+  return sweep;  // rotation sweeps performed
 }
 
 // Sort eigenpairs by decreasing eigenvalue: lam[r] and column r of Vout.
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
   __syncthreads();
 
   // 2. G_v = W lam W^H.
-  jacobi_eig(Gv, Z, n, a.max_sweeps, sh, rc, rs, rph);
+  const int sweeps_v = jacobi_eig(Gv, Z, n, a.max_sweeps, sh, rc, rs, rph);
   sort_eig(Gv, Z, W, n, lam, perm);
   const double lmax = lam[0] > 0.0 ? lam[0] : 0.0;
   const double lcut = a.gram_cut * lmax;
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
   __syncthreads();
 
   // 4. H = U diag(sigma^2) U^H.
-  jacobi_eig(H, Z, n, a.max_sweeps, sh, rc, rs, rph);
+  const int sweeps_h = jacobi_eig(H, Z, n, a.max_sweeps, sh, rc, rs, rph);
   sort_eig(H, Z, U, n, sig, perm);
 
   // 5. Truncation to chi and normalisation (thread 0; n <= 512 values).
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
     st[0] = tot > 0.0 ? (tot - kept) / tot : 0.0;
     st[1] = nk;
     st[2] = s0;
-    st[3] = 0.0;
+    st[3] = sweeps_v + sweeps_h;
     if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(a.flags, 1);
   }
   __syncthreads();

@@ -36,7 +36,6 @@ constexpr int kThreads = 1024;
 
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChi = 64;
-constexpr float kOrthTol = 2e-6f;
 constexpr double kAbsTol = 1e-12;
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -159,6 +158,7 @@ struct Smem {
   double* scal;    // 4
   double* red_d;   // 32
   float2* colk;    // n
+  float* nrm;      // n: squared row norms during the Jacobi
 };
 
 __device__ Smem carve(unsigned char* base, int chi) {
@@ -171,6 +171,7 @@ __device__ Smem carve(unsigned char* base, int chi) {
   s.scal = reinterpret_cast<double*>(p); p += sizeof(double) * 4;
   s.red_d = reinterpret_cast<double*>(p); p += sizeof(double) * 32;
   s.colk = reinterpret_cast<float2*>(p); p += sizeof(float2) * n;
+  s.nrm = reinterpret_cast<float*>(p); p += sizeof(float) * n;
   s.perm_w = reinterpret_cast<int*>(p); p += sizeof(int) * n;
   s.perm_v = reinterpret_cast<int*>(p); p += sizeof(int) * 2 * chi;
   s.src = reinterpret_cast<int*>(p); p += sizeof(int) * n;
@@ -308,8 +309,98 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     __syncthreads();
   }
   const float abs_floor = (float)(kAbsTol * s.scal[2]);
+  const float orth_tol = a.orth_tol > 0.f ? a.orth_tol : 2e-6f;
   const int half = n / 2;
+  int sweeps = 0;
+  if (n % 32 == 0) {
+    // Rows of 2 x 16-byte vectors: each pair is owned by 16 lanes (two pairs per
+    // warp, so the rotation arithmetic serves two pairs), lane l holding the
+    // vectors l, l + 16, ... of both rows (consecutive lanes, consecutive
+    // addresses).  Squared row norms live in shared memory: recomputed exactly
+    // at the start of each sweep and updated by each rotation, which moves
+    // t |gamma| of weight from row p to row q (alpha' = alpha - t|g|,
+    // beta' = beta + t|g|).
+    float4* X4 = reinterpret_cast<float4*>(X);
+    const int row4 = n / 2, nq = n / 32;
+    const int sub = lane >> 4, gl = lane & 15;
+    for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+      ++sweeps;
+      for (int j = warp; j < n; j += kWarps) {
+        float acc = 0.f;
+        for (int c = lane; c < row4; c += 32) {
+          const float4 v = X4[j * row4 + c];
+          acc += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) s.nrm[j] = acc;
+      }
+      __syncthreads();
+      int any = 0;
+      for (int r = 0; r < n - 1; ++r) {
+        const int k = warp * 2 + sub;
+        int rot = 0;
+        if (2 * warp < half) {  // warp-uniform: half is even
+          int p, q;
+          if (k == 0) { p = r; q = n - 1; }
+          else { p = (r + k) % (n - 1); q = (r - k + (n - 1)) % (n - 1); }
+          // (the rows are read twice, for gamma and for the rotation, to stay
+          // within the 64 registers a thread of a 1024-thread block has)
+          float gr = 0.f, gi = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (u < nq) {
+              const float4 xp = X4[p * row4 + gl + 16 * u];
+              const float4 xq = X4[q * row4 + gl + 16 * u];
+              // gamma = sum conj(xp) xq over the two complex values of the vector
+              gr += xp.x * xq.x + xp.y * xq.y + xp.z * xq.z + xp.w * xq.w;
+              gi += xp.x * xq.y - xp.y * xq.x + xp.z * xq.w - xp.w * xq.z;
+            }
+          }
+#pragma unroll
+          for (int o = 8; o > 0; o >>= 1) {
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gi += __shfl_xor_sync(0xffffffffu, gi, o);
+          }
+          const float al = s.nrm[p], be = s.nrm[q];
+          const float gm = sqrtf(gr * gr + gi * gi);
+          if (gm > orth_tol * sqrtf(al * be) && gm > abs_floor && gm > 0.f) {
+            const float igm = 1.f / gm;
+            const float2 ph = make_float2(gr * igm, -gi * igm);  // e^{-i phi}
+            const float tau = (be - al) * 0.5f * igm;
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            // exactly rounded: an approximate reciprocal square root makes every
+            // rotation slightly non-unitary and the row norms drift
+            const float cs = 1.f / sqrtf(1.f + t * t);
+            const float sn = t * cs;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (u < nq) {
+                const float4 xp = X4[p * row4 + gl + 16 * u];
+                const float4 xq = X4[q * row4 + gl + 16 * u];
+                const float2 q0 = cmulf(ph, make_float2(xq.x, xq.y));
+                const float2 q1 = cmulf(ph, make_float2(xq.z, xq.w));
+                X4[p * row4 + gl + 16 * u] =
+                    make_float4(cs * xp.x - sn * q0.x, cs * xp.y - sn * q0.y,
+                                cs * xp.z - sn * q1.x, cs * xp.w - sn * q1.y);
+                X4[q * row4 + gl + 16 * u] =
+                    make_float4(sn * xp.x + cs * q0.x, sn * xp.y + cs * q0.y,
+                                sn * xp.z + cs * q1.x, sn * xp.w + cs * q1.y);
+              }
+            }
+            if (gl == 0) {
+              s.nrm[p] = fmaxf(al - t * gm, 0.f);
+              s.nrm[q] = be + t * gm;
+            }
+            rot = 1;
+          }
+        }
+        any |= __syncthreads_or(rot);
+      }
+      if (!any) break;
+    }
+  } else
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    ++sweeps;
     if (tid == 0) s.counter[0] = 0;
     __syncthreads();
     for (int r = 0; r < n - 1; ++r) {
@@ -341,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
         const float gm = sqrtf(gr * gr + gi * gi);
         // pairs already orthogonal to FP32 precision are left alone; a sweep
         // that rotates no pair ends the iteration
-        if (gm > kOrthTol * sqrtf(al * be) && gm > abs_floor && gm > 0.f) {
+        if (gm > orth_tol * sqrtf(al * be) && gm > abs_floor && gm > 0.f) {
           const float2 ph = make_float2(gr / gm, -gi / gm);  // e^{-i phi}, gamma = |g| e^{i phi}
           const float tau = (be - al) / (2.f * gm);
           const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
@@ -403,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     st[0] = tot > 0.0 ? (tot - kept) / tot : 0.0;
     st[1] = nk;
     st[2] = s0;
-    st[3] = 0.0;
+    st[3] = sweeps;
     if (!(kept > 0.0) || !isfinite(kept)) atomicOr(a.flags, 1);
   }
   __syncthreads();
@@ -529,7 +620,8 @@ size_t smem_bytes(int chi) {
   const int n = 2 * chi;
   return sizeof(float2) * (size_t)n * n + sizeof(float2) * 2 * chi * chi + sizeof(double) * (n + 4 + 32) +
          sizeof(double) * 2 * n +
-         sizeof(int) * (n + 2 * chi + n + n + 4 + 32) + sizeof(float) * (32 + 4) + sizeof(int) * 4 + 64;
+         sizeof(int) * (n + 2 * chi + n + n + 4 + 32) + sizeof(float) * (32 + 4) + sizeof(int) * 4 +
+         sizeof(float) * n + 64;
 }
 
 }  // namespace
