@@ -395,10 +395,14 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
   for (auto& L : P.L) {
     const int pi = prof_begin(h, cls);
     int nk = 1;
+    // contractions too small to fill a tensor-core tile pipeline (the
+    // degree-1 closes: chi^2 outputs over K = 2) run on the CUDA cores in FP32
+    const double macs = (double)L.d.n_outer * L.d.n_inner * L.d.M * L.d.N * L.d.K1 * L.d.K2;
+    const bool tiny = macs < 262144.0;
     if (L.sp.maps) {
       TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, h->stream));
       h->stats.tma_launches++;
-    } else if (use_tensor_cores(h)) {
+    } else if (use_tensor_cores(h) && !tiny) {
       TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, h->stream, &nk));
     } else {
       TN_CUDA_TRY(launch_cgemm(L.d, h->stream));

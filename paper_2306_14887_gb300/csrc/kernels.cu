@@ -230,18 +230,27 @@ __global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
 __global__ void normalise_kernel(const float* raw, float* msg, int chi,
                                  unsigned long long* res_bits, int* flags, float* mrt) {
   __shared__ double sh[32];
-  extern __shared__ float sraw[];  // 2 chi^2: re plane, im plane
+  extern __shared__ float sraw[];  // re plane, im plane: chi x (chi + 1) each (padded rows)
+  const int ld = chi + 1;
   const int64_t n2 = (int64_t)chi * chi;
+  float* sre = sraw;
+  float* sim = sraw + (int64_t)chi * ld;
   const float* r = raw + blockIdx.x * 2 * n2;
   float* m = msg + blockIdx.x * 2 * n2;
-  for (int64_t idx = threadIdx.x; idx < 2 * n2; idx += blockDim.x) sraw[idx] = r[idx];
+  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
+    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
+    sre[i * ld + j] = r[idx];
+    sim[i * ld + j] = r[n2 + idx];
+  }
   __syncthreads();
+  // H = (R + R^H) / 2: element (i, j) with the transposed read from the padded
+  // tile (consecutive threads, consecutive j: distinct banks)
   double ss = 0.0;
   for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
     const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    const double hr = 0.5 * ((double)sraw[idx] + (double)sraw[(int64_t)j * chi + i]);
-    const double hi = 0.5 * ((double)sraw[n2 + idx] - (double)sraw[n2 + (int64_t)j * chi + i]);
-    ss += hr * hr + hi * hi;
+    const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]);
+    const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]);
+    ss += (double)hr * hr + (double)hi * hi;
   }
   ss = block_sum(ss, sh);
   const double nrm = sqrt(ss);
@@ -249,26 +258,27 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
     if (threadIdx.x == 0) atomicOr(flags, 1);
     return;
   }
-  const double inv = 1.0 / nrm;
+  const float inv = (float)(1.0 / nrm);
   double dd = 0.0;
+  float* q = mrt ? mrt + (int64_t)blockIdx.x * 4 * n2 : nullptr;
+  const int64_t w = 2 * chi;
   for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
     const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    const double hr = 0.5 * ((double)sraw[idx] + (double)sraw[(int64_t)j * chi + i]) * inv;
-    const double hi = 0.5 * ((double)sraw[n2 + idx] - (double)sraw[n2 + (int64_t)j * chi + i]) * inv;
-    const double er = hr - (double)m[idx], ei = hi - (double)m[n2 + idx];
+    const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]) * inv;
+    const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]) * inv;
+    const double er = (double)hr - (double)m[idx], ei = (double)hi - (double)m[n2 + idx];
     dd += er * er + ei * ei;
-    m[idx] = (float)hr;
-    m[n2 + idx] = (float)hi;
-    if (mrt) {
-      // realified transpose: row (t, n), column (s, k) of a [2chi][2chi] matrix;
-      // the message element [k][n] = (i, j) goes to (0,j)(0,i), (1,j)(1,i) as re,
-      // (1,j)(0,i) as +im and (0,j)(1,i) as -im
-      float* q = mrt + (int64_t)blockIdx.x * 4 * n2;
-      const int64_t w = 2 * chi;
-      q[(int64_t)j * w + i] = (float)hr;
-      q[(int64_t)(chi + j) * w + chi + i] = (float)hr;
-      q[(int64_t)(chi + j) * w + i] = (float)hi;
-      q[(int64_t)j * w + chi + i] = (float)-hi;
+    m[idx] = hr;
+    m[n2 + idx] = hi;
+    if (q) {
+      // realified transpose of the message: a [2chi][2chi] matrix with row (t, n)
+      // and column (s, k), [[Re, Im], [-Im, Re]] of M[k][n] read transposed.
+      // H is Hermitian, so M[k = j][n = i] = conj(H[i][j]): row i, column j is
+      // written from this thread's own element (row-contiguous stores).
+      q[(int64_t)i * w + j] = hr;
+      q[(int64_t)(chi + i) * w + chi + j] = hr;
+      q[(int64_t)(chi + i) * w + j] = -hi;
+      q[(int64_t)i * w + chi + j] = hi;
     }
   }
   dd = block_sum(dd, sh);
@@ -295,20 +305,30 @@ __global__ void realify_kernel(const float* src, int64_t stride, float* dst, int
   }
 }
 
-// TA[pl][p][rest][l0] = T[pl][p][l0][rest]: one CTA row per (site, plane, p, l0)
-// block of `rest` = chi^(d-1) contiguous elements.
-__global__ void first_leg_last_kernel(const float* T, float* TA, const int64_t* site_off, int d,
+// TA[pl][p][rest][l0] = T[pl][p][l0][rest]: per (site, plane, p) a chi x rest
+// matrix transposed through a padded 32 x 33 shared tile, so that both the
+// reads (along rest) and the writes (along l0) are row-contiguous.
+__global__ void first_leg_last_kernel(const float* T, float* TA, const int64_t* site_off,
                                       int chi, int64_t rest) {
-  const int site = blockIdx.y;
+  __shared__ float tile[32][33];
+  const int site = blockIdx.z >> 2, pp = blockIdx.z & 3;  // pp = plane * 2 + p
   const int64_t len = rest * chi;  // chi^d
-  const float* src = T + site_off[site];
-  float* dst = TA + site_off[site];
-  const int blk = blockIdx.x;      // (plane, p, l0) in 0 .. 4 chi
-  const int l0 = blk % chi;
-  const int pp = blk / chi;        // plane * 2 + p
-  const float* s = src + (int64_t)pp * len + (int64_t)l0 * rest;
-  float* q = dst + (int64_t)pp * len + l0;
-  for (int64_t r = threadIdx.x; r < rest; r += blockDim.x) q[r * chi] = s[r];
+  const float* src = T + site_off[site] + (int64_t)pp * len;  // [l0][rest]
+  float* dst = TA + site_off[site] + (int64_t)pp * len;       // [rest][l0]
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int l00 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 32; i += 8) {
+    const int l0 = l00 + i;
+    const int64_t r = r0 + tx;
+    if (l0 < chi && r < rest) tile[i][tx] = src[(int64_t)l0 * rest + r];
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i;
+    const int l0 = l00 + tx;
+    if (r < rest && l0 < chi) dst[r * chi + l0] = tile[tx][i];
+  }
 }
 }  // namespace
 
@@ -328,15 +348,16 @@ cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site
   if (n_sites <= 0 || d < 2) return cudaSuccess;
   int64_t rest = 1;
   for (int i = 1; i < d; ++i) rest *= chi;
-  dim3 grid(4 * chi, n_sites);
-  first_leg_last_kernel<<<grid, 128, 0, s>>>(T, TA, site_off, d, chi, rest);
+  if (4LL * n_sites > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((rest + 31) / 32), (unsigned)((chi + 31) / 32), (unsigned)(4 * n_sites));
+  first_leg_last_kernel<<<grid, dim3(32, 8), 0, s>>>(T, TA, site_off, chi, rest);
   return cudaGetLastError();
 }
 
 static int g_norm_attr_bytes = 48 * 1024;
 
 cudaError_t normalise_prepare(int chi) {
-  const size_t sm = sizeof(float) * 2 * (size_t)chi * chi;
+  const size_t sm = sizeof(float) * 2 * (size_t)chi * (chi + 1);
   if (sm > 200 * 1024 || (int)sm <= g_norm_attr_bytes) return cudaSuccess;
   cudaError_t e =
       cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -347,7 +368,7 @@ cudaError_t normalise_prepare(int chi) {
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
                              unsigned long long* res_bits, int* flags, cudaStream_t s, float* mrt) {
   if (n_msgs <= 0) return cudaSuccess;
-  const size_t sm = sizeof(float) * 2 * (size_t)chi * chi;
+  const size_t sm = sizeof(float) * 2 * (size_t)chi * (chi + 1);
   if (sm > 200 * 1024) {
     normalise_gmem_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags);
     cudaError_t e = cudaGetLastError();
