@@ -89,8 +89,11 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
 // tensor map per batch entry, encoded on the host when a plan is uploaded.
 struct TcStreamPlan {
   const void* maps = nullptr;  // device CUtensorMap[2 * n_outer]
+  int kind = 0;                // 0: mode product (streaming), 1: close (TMA split-K)
   int n_outer = 0, rank = 0, lev0 = 1, lev1 = 1;
+  int splits = 1;              // close: K splits per entry
 };
+cudaError_t launch_tc_reduce(const GemmDesc& d, const float* part, int splits, cudaStream_t s);
 // Fills host_maps (tc_stream_map_bytes(n_outer) bytes, 64-byte aligned) and
 // the plan's shape fields; false when the descriptor is not eligible.
 bool tc_stream_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
@@ -98,6 +101,13 @@ bool tc_stream_encode(const GemmDesc& d, const float* const* A, const float* con
 size_t tc_stream_map_bytes(int n_outer);
 cudaError_t tc_stream_prepare();
 cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err, cudaStream_t s);
+// Closes (tc_stream.cu): out[m][n] = sum_K A[m][K] op(B[n][K]), M = N = 64, both
+// operands K-contiguous, TF32; TMA-fed split-K into partials + the fixed-order
+// reduce.  part_floats bounds the partial buffer the caller provides.
+bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
+                     size_t part_floats, void* host_maps, TcStreamPlan* p);
+cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* part, int* err,
+                            cudaStream_t s);
 // Kernel attributes set once, before any launch or stream capture.
 cudaError_t tc_prepare();
 cudaError_t normalise_prepare(int chi);

@@ -122,6 +122,7 @@ struct tn_handle {
   cudaGraphExec_t sweep_exec = nullptr;
   double sweep_flops = 0.0, sweep_bytes = 0.0;
   int64_t sweep_kernels = 0, sweep_tma = 0;  // launches inside the captured sweep
+  size_t part_floats = 0;                     // size of the split-K partial buffer
   unsigned long long* h_status = nullptr;  // pinned: [residual bits, flags]
 
   // per-kernel-class timing with CUDA events on the handle's stream
@@ -300,7 +301,9 @@ tn_status upload_plans(tn_handle* h) {
     for (Plan* p : plans)
       for (auto& L : p->L) {
         TcStreamPlan sp;
-        if (tc_stream_encode(L.d, L.A.data(), L.B.data(), (int)L.A.size(), base + mpos, &sp)) {
+        if (tc_stream_encode(L.d, L.A.data(), L.B.data(), (int)L.A.size(), base + mpos, &sp) ||
+            tc_close_encode(L.d, L.A.data(), L.B.data(), (int)L.A.size(), h->part_floats,
+                            base + mpos, &sp)) {
           L.sp = sp;
           users.push_back(&L);
           offs.push_back(mpos);
@@ -399,7 +402,11 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
     // degree-1 closes: chi^2 outputs over K = 2) run on the CUDA cores in FP32
     const double macs = (double)L.d.n_outer * L.d.n_inner * L.d.M * L.d.N * L.d.K1 * L.d.K2;
     const bool tiny = macs < 262144.0;
-    if (L.sp.maps) {
+    if (L.sp.maps && L.sp.kind == 1) {
+      TN_CUDA_TRY(launch_tc_close(L.d, L.sp, h->part, h->flags, h->stream));
+      h->stats.tma_launches++;
+      nk = 2;
+    } else if (L.sp.maps) {
       TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, h->stream));
       h->stats.tma_launches++;
     } else if (use_tensor_cores(h) && !tiny) {
@@ -1288,7 +1295,10 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
         tc_plan(L.d, &q, &sp, &pf);
         need = std::max(need, pf);
       }
-    h->part = (float*)dev_alloc(h, sizeof(float) * std::max<size_t>(need, 16));
+    // the TMA closes take at most 2 x 152 CTAs of partials over the entries
+    need = std::max<size_t>(need, (size_t)2 * 2 * 152 * 2 * 4096);
+    h->part_floats = std::max<size_t>(need, 16);
+    h->part = (float*)dev_alloc(h, sizeof(float) * h->part_floats);
     if (!h->part) { delete[] h->h_stats; set_error("device allocation failed"); return fail(TN_ENOMEM); }
   }
   tn_status st = upload_plans(h);

@@ -232,26 +232,28 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
   __shared__ double sh[32];
   extern __shared__ float sraw[];  // re plane, im plane: chi x (chi + 1) each (padded rows)
   const int ld = chi + 1;
-  const int64_t n2 = (int64_t)chi * chi;
+  const int n2 = chi * chi;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float* sre = sraw;
-  float* sim = sraw + (int64_t)chi * ld;
-  const float* r = raw + blockIdx.x * 2 * n2;
-  float* m = msg + blockIdx.x * 2 * n2;
-  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
-    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    sre[i * ld + j] = r[idx];
-    sim[i * ld + j] = r[n2 + idx];
-  }
+  float* sim = sraw + chi * ld;
+  const float* r = raw + (int64_t)blockIdx.x * 2 * n2;
+  float* m = msg + (int64_t)blockIdx.x * 2 * n2;
+  // rows i over warps, columns j over lanes: no index division
+  for (int i = warp; i < chi; i += nw)
+    for (int j = lane; j < chi; j += 32) {
+      sre[i * ld + j] = r[i * chi + j];
+      sim[i * ld + j] = r[n2 + i * chi + j];
+    }
   __syncthreads();
   // H = (R + R^H) / 2: element (i, j) with the transposed read from the padded
-  // tile (consecutive threads, consecutive j: distinct banks)
+  // tile (consecutive lanes, consecutive j: distinct banks); sums in FP64
   double ss = 0.0;
-  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
-    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]);
-    const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]);
-    ss += (double)hr * hr + (double)hi * hi;
-  }
+  for (int i = warp; i < chi; i += nw)
+    for (int j = lane; j < chi; j += 32) {
+      const double hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]);
+      const double hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]);
+      ss = fma(hr, hr, fma(hi, hi, ss));
+    }
   ss = block_sum(ss, sh);
   const double nrm = sqrt(ss);
   if (!(nrm > 0.0) || !isfinite(nrm)) {
@@ -261,26 +263,28 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
   const float inv = (float)(1.0 / nrm);
   double dd = 0.0;
   float* q = mrt ? mrt + (int64_t)blockIdx.x * 4 * n2 : nullptr;
-  const int64_t w = 2 * chi;
-  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
-    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]) * inv;
-    const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]) * inv;
-    const double er = (double)hr - (double)m[idx], ei = (double)hi - (double)m[n2 + idx];
-    dd += er * er + ei * ei;
-    m[idx] = hr;
-    m[n2 + idx] = hi;
-    if (q) {
-      // realified transpose of the message: a [2chi][2chi] matrix with row (t, n)
-      // and column (s, k), [[Re, Im], [-Im, Re]] of M[k][n] read transposed.
-      // H is Hermitian, so M[k = j][n = i] = conj(H[i][j]): row i, column j is
-      // written from this thread's own element (row-contiguous stores).
-      q[(int64_t)i * w + j] = hr;
-      q[(int64_t)(chi + i) * w + chi + j] = hr;
-      q[(int64_t)(chi + i) * w + j] = -hi;
-      q[(int64_t)i * w + chi + j] = hi;
+  const int w = 2 * chi;
+  for (int i = warp; i < chi; i += nw)
+    for (int j = lane; j < chi; j += 32) {
+      const int idx = i * chi + j;
+      const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]) * inv;
+      const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]) * inv;
+      // the difference of two nearby FP32 values is exact; squared and summed in FP64
+      const double er = hr - m[idx], ei = hi - m[n2 + idx];
+      dd = fma(er, er, fma(ei, ei, dd));
+      m[idx] = hr;
+      m[n2 + idx] = hi;
+      if (q) {
+        // realified transpose of the message: a [2chi][2chi] matrix with row (t, n)
+        // and column (s, k), [[Re, Im], [-Im, Re]] of M[k][n] read transposed.
+        // H is Hermitian, so M[k = j][n = i] = conj(H[i][j]): row i, column j is
+        // written from this thread's own element (row-contiguous stores).
+        q[i * w + j] = hr;
+        q[(chi + i) * w + chi + j] = hr;
+        q[(chi + i) * w + j] = -hi;
+        q[i * w + chi + j] = hi;
+      }
     }
-  }
   dd = block_sum(dd, sh);
   if (threadIdx.x == 0) {
     const double res = sqrt(dd);

@@ -538,6 +538,13 @@ __global__ void tc_reduce_kernel(GemmDesc d, const float* part, int splits) {
 
 size_t tc_smem_bytes() { return TcSmem::kBytes + 1024; }
 
+// Sum split-K partials [split][outer][inner][re|im][M][N] into C in a fixed order.
+cudaError_t launch_tc_reduce(const GemmDesc& d, const float* part, int splits, cudaStream_t st) {
+  dim3 rg((d.M * d.N + 255) / 256, d.n_outer * d.n_inner);
+  tc_reduce_kernel<<<rg, 256, 0, st>>>(d, part, splits);
+  return cudaGetLastError();
+}
+
 // Plan a tensor-core launch for d: quad form when the contraction is long and
 // M, N small (2M <= 128), else realified-B form.
 bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {

@@ -283,6 +283,142 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
   }
 }
 
+// ---------------------------------------------------------------- closes
+// out[m][n] = sum_K A[m][K] op(B[n][K]) with M = N = 64 (the message's two
+// indices), both operands K-contiguous site tensors: per K chunk of 32 the
+// tile is [(s, m)][32] of A and [(t, n)][32] of B (s, t the re/im planes, so
+// the 128 x 128 product holds all four real products P_st), streamed by TMA
+// through a 3-stage ring; K is split over CTAs, two CTAs per SM.  The
+// epilogue stages P in shared memory, combines C_re = P_rr - sa sb P_ii,
+// C_im = sb P_ri + sa P_ir and writes the CTA's partial; a second kernel sums
+// the partials in a fixed order.
+constexpr int kCThreads = 192;
+constexpr int kCStages = 3;
+constexpr int kCStage = 2 * kChunk;  // A 16 KB + B 16 KB
+constexpr int kCBarOff = kCStages * kCStage;
+constexpr int kCSmemBytes = kCBarOff + 128 + 1024;
+
+struct CloseArgs {
+  const CUtensorMap* maps;  // [2 * n_outer]: A maps, then B maps
+  int n_outer, chunks, per_split, K2;
+  float* part;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, CloseArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCBarOff);
+  uint64_t* empty = full + kCStages;
+  uint64_t* accum = empty + kCStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int e = blockIdx.y, split = blockIdx.x;
+  const int c0 = split * a.per_split;
+  const int c1 = min(a.chunks, c0 + a.per_split);
+  const int nt = c1 > c0 ? c1 - c0 : 0;  // >= 1 by the host's choice of splits
+
+  if (tid == 0) {
+    for (int s = 0; s < kCStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const CUtensorMap* amap = a.maps + e;
+  const CUtensorMap* bmap = a.maps + a.n_outer + e;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued[kCStages] = {0, 0, 0};
+      for (int i = 0; i < nt && !*abort_flag; ++i) {
+        const int slot = i % kCStages;
+        if (!mbar_wait(&empty[slot], ((i / kCStages) & 1) ^ 1, a.err)) { *abort_flag = 1; break; }
+        mbar_expect_tx(&full[slot], (uint32_t)(2 * kChunk));
+        const int k = (c0 + i) * 32;
+        const int k1 = k / a.K2, k2 = k - k1 * a.K2;
+        const uint32_t dst = smem_u32(smem + slot * kCStage);
+        tma_load_4d(dst, amap, k2, 0, k1, 0, &full[slot]);
+        tma_load_4d(dst + kChunk, bmap, k2, 0, k1, 0, &full[slot]);
+        ++issued[slot];
+      }
+      for (int s = 0; s < kCStages; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (issued[s] - 1) & 1, a.err);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(2, 128, 128);
+      for (int i = 0; i < nt && !*abort_flag; ++i) {
+        const int slot = i % kCStages;
+        if (!mbar_wait(&full[slot], (i / kCStages) & 1, a.err)) { *abort_flag = 1; break; }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + slot * kCStage);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          mma_issue(0, tmem, sw128_desc(a0 + ks * 32), sw128_desc(a0 + kChunk + ks * 32), idesc,
+                    (i > 0 || ks > 0) ? 1u : 0u);
+        mma_commit(&empty[slot]);
+      }
+      mma_commit(accum);  // also orders TMEM release after every MMA issued
+    }
+    __syncwarp();
+  }
+  // every thread: the accumulator is final (or the CTA gave up)
+  const bool ok = mbar_wait(accum, 0, a.err) && !*abort_flag && nt > 0;
+  tc_fence_after();
+  if (warp >= 2) {
+    // P staged in the (now idle) pipeline buffers: [128 rows][129]
+    float* P = reinterpret_cast<float*>(smem);
+    const int q = warp & 3, row = q * 32 + lane;
+#pragma unroll
+    for (int c = 0; c < 128; c += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) P[row * 129 + c + j] = v[j];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const float sa = d.conj_a ? -1.f : 1.f, sb = d.conj_b ? -1.f : 1.f;
+    float* out = a.part + ((int64_t)split * a.n_outer + e) * 2 * 4096;
+    for (int idx = tid - 64; idx < 4096; idx += 128) {
+      const int m = idx >> 6, n = idx & 63;
+      float cr = 0.f, ci = 0.f;
+      if (ok) {
+        const float prr = P[m * 129 + n], pii = P[(64 + m) * 129 + 64 + n];
+        const float pri = P[m * 129 + 64 + n], pir = P[(64 + m) * 129 + n];
+        cr = prr - sa * sb * pii;
+        ci = sb * pri + sa * pir;
+      }
+      out[idx] = cr;
+      out[4096 + idx] = ci;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+                 : "memory");
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -452,6 +588,78 @@ cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err,
   const int grid = total < g_num_sms ? total : g_num_sms;
   tc_stream_kernel<<<grid, kThreads, kSmemBytes, st>>>(d, a);
   return cudaGetLastError();
+}
+
+
+bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
+                     size_t part_floats, void* host_maps, TcStreamPlan* p) {
+  if (d.prec != TN_TF32 || d.b_pre || d.M != 64 || d.N != 64 || d.a_k2 != 1 || d.b_k2 != 1 ||
+      d.n_inner != 1 || d.K2 % 32 || d.M2 > 1 || d.M3 > 1 || d.accumulate || n_outer < 1)
+    return false;
+  if (tc_stream_prepare() != cudaSuccess) return false;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int64_t s_a[3] = {d.a_m, d.K1 > 1 ? d.a_k1 : d.plane_a, d.plane_a};
+  const int64_t s_b[3] = {d.b_n, d.K1 > 1 ? d.b_k1 : d.plane_b, d.plane_b};
+  for (int i = 0; i < 3; ++i)
+    if (s_a[i] <= 0 || s_b[i] <= 0 || (s_a[i] * 4) % 16 || (s_b[i] * 4) % 16) return false;
+  const int chunks = d.K1 * d.K2 / 32;
+  int S = 1;
+  while ((int64_t)n_outer * S * 2 <= 2LL * g_num_sms && chunks / (S * 2) >= 4) S *= 2;
+  const int per = (chunks + S - 1) / S;
+  S = (chunks + per - 1) / per;  // every split holds at least one chunk
+  if ((size_t)S * n_outer * 2 * 4096 > part_floats) return false;
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host_maps);
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t box[4] = {32, 64, 1, 2};
+  for (int e = 0; e < n_outer; ++e) {
+    if ((reinterpret_cast<uintptr_t>(A[e]) & 15) || (reinterpret_cast<uintptr_t>(B[e]) & 15))
+      return false;
+    cuuint64_t dims[4] = {(cuuint64_t)d.K2, 64, (cuuint64_t)d.K1, 2};
+    cuuint64_t sa[3] = {(cuuint64_t)(s_a[0] * 4), (cuuint64_t)(s_a[1] * 4),
+                        (cuuint64_t)(s_a[2] * 4)};
+    cuuint64_t sb[3] = {(cuuint64_t)(s_b[0] * 4), (cuuint64_t)(s_b[1] * 4),
+                        (cuuint64_t)(s_b[2] * 4)};
+    if (enc(&maps[e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(A[e]), dims, sa, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    if (enc(&maps[n_outer + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(B[e]), dims,
+            sb, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  p->kind = 1;
+  p->n_outer = n_outer;
+  p->splits = S;
+  p->rank = 4;
+  return true;
+}
+
+cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* part, int* err,
+                            cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_close_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_close_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CloseArgs a;
+  a.maps = reinterpret_cast<const CUtensorMap*>(p.maps);
+  a.n_outer = p.n_outer;
+  a.chunks = d.K1 * d.K2 / 32;
+  a.per_split = (a.chunks + p.splits - 1) / p.splits;
+  a.K2 = d.K2;
+  a.part = part;
+  a.err = err;
+  dim3 grid(p.splits, p.n_outer);
+  tc_close_kernel<<<grid, kCThreads, kCSmemBytes, st>>>(d, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_tc_reduce(d, part, p.splits, st);
 }
 
 }  // namespace tnbp
