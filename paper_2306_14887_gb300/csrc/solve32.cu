@@ -55,96 +55,114 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
+// A group of threads [t0, t0 + nt) of the block synchronised by a named barrier.
+struct Group {
+  int t0, nt, bar;
+  __device__ int tid() const { return (int)threadIdx.x - t0; }
+  __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory"); }
+};
+
 // Pivoted Cholesky of the Hermitian PSD m x m matrix A (row stride ld, full
-// storage) in place, FP32 in shared memory: afterwards A's lower triangle holds
-// L with P^T A P = L L^H, perm[t] = original index of pivot t, and *rank the
-// number of pivots above rel_tol * (largest initial diagonal); everything
-// outside the first `rank` columns of the lower triangle is zeroed.  The
-// trailing update keeps the full Hermitian block current, so each pivot's row
-// and column exchange reads current values.
+// storage) in place, FP32 in shared memory, by the threads of group g:
+// afterwards A's lower triangle holds L with P^T A P = L L^H, perm[t] =
+// original index of pivot t, and *rank the number of pivots above
+// rel_tol * (largest initial diagonal); everything outside the first `rank`
+// columns of the lower triangle is zeroed.  The trailing update keeps the full
+// Hermitian block current, so each pivot's row and column exchange reads
+// current values.  Per pivot: the group's first warp finds the pivot, one pass
+// applies the symmetric exchange, one scales the column, one updates the
+// trailing block (rows over warps, columns over lanes).
 __device__ void pivoted_cholesky32(float2* A, int m, int ld, int* perm, float rel_tol, int* rank,
-                                   float* red_v, int* red_i, float* dmax0, float2* colk) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < m; i += blockDim.x) perm[i] = i;
-  __syncthreads();
+                                   int* piv_s, float* pv_s, float* dmax0, float2* colk,
+                                   const Group& g) {
+  const int tid = g.tid(), lane = tid & 31, warp = tid >> 5, nw = g.nt >> 5;
+  for (int i = tid; i < m; i += g.nt) perm[i] = i;
+  g.sync();
   int r = m;
   for (int k = 0; k < m; ++k) {
-    float best = -1.f;
-    int bi = k;
-    for (int i = k + tid; i < m; i += blockDim.x) {
-      const float d = A[i * ld + i].x;
-      if (d > best) { best = d; bi = i; }
+    if (warp == 0) {
+      float best = -1.f;
+      int bi = k;
+      for (int i = k + lane; i < m; i += 32) {
+        const float d = A[i * ld + i].x;
+        if (d > best) { best = d; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        *pv_s = best;
+        *piv_s = bi;
+        if (k == 0) *dmax0 = best > 0.f ? best : 0.f;
+      }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      float b = red_v[0];
-      int ii = red_i[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (red_v[w] > b || (red_v[w] == b && red_i[w] < ii)) { b = red_v[w]; ii = red_i[w]; }
-      red_v[0] = b;
-      red_i[0] = ii;
-      if (k == 0) *dmax0 = b > 0.f ? b : 0.f;
-    }
-    __syncthreads();
-    const float pv = red_v[0];
-    const int piv = red_i[0];
+    g.sync();
+    const float pv = *pv_s;
+    const int piv = *piv_s;
     const float d0 = *dmax0;
-    __syncthreads();
     if (!(d0 > 0.f) || !(pv > rel_tol * d0)) { r = k; break; }
     if (piv != k) {
-      for (int j = tid; j < m; j += blockDim.x) {
+      // symmetric exchange of rows / columns k and piv: rows over all columns
+      // (the L part included), columns over the trailing rows, the 2 x 2 block
+      // {k, piv} by one thread
+      for (int j = tid; j < m; j += g.nt) {
+        if (j == k || j == piv) continue;
         const float2 t = A[k * ld + j];
         A[k * ld + j] = A[piv * ld + j];
         A[piv * ld + j] = t;
+        if (j > k) {
+          const float2 u = A[j * ld + k];
+          A[j * ld + k] = A[j * ld + piv];
+          A[j * ld + piv] = u;
+        }
       }
-      __syncthreads();
-      for (int i = tid; i < m; i += blockDim.x) {
-        const float2 t = A[i * ld + k];
-        A[i * ld + k] = A[i * ld + piv];
-        A[i * ld + piv] = t;
+      if (tid == 0) {
+        const float2 kk = A[k * ld + k], pp = A[piv * ld + piv];
+        const float2 kp = A[k * ld + piv], pk = A[piv * ld + k];
+        A[k * ld + k] = pp;
+        A[piv * ld + piv] = kk;
+        A[k * ld + piv] = pk;
+        A[piv * ld + k] = kp;
+        const int t = perm[k];
+        perm[k] = perm[piv];
+        perm[piv] = t;
       }
-      if (tid == 0) { const int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t; }
-      __syncthreads();
+      g.sync();
     }
     const float d = sqrtf(A[k * ld + k].x);
     const float inv = 1.f / d;
-    __syncthreads();
-    for (int i = k + 1 + tid; i < m; i += blockDim.x) {
+    for (int i = k + 1 + tid; i < m; i += g.nt) {
       const float2 a = A[i * ld + k];
       const float2 l = make_float2(a.x * inv, a.y * inv);
       A[i * ld + k] = l;
       colk[i] = l;
     }
-    __syncthreads();
+    g.sync();
     if (tid == 0) A[k * ld + k] = make_float2(d, 0.f);
-    const int rem = m - k - 1;
-    for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
-      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-      const float2 p = cmulf(colk[i], cconjf(colk[j]));
-      float2 a = A[i * ld + j];
-      a.x -= p.x;
-      a.y -= p.y;
-      A[i * ld + j] = a;
+    for (int i = k + 1 + warp; i < m; i += nw) {
+      const float2 ci = colk[i];
+      for (int j = k + 1 + lane; j < m; j += 32) {
+        const float2 cj = colk[j];
+        float2 a = A[i * ld + j];
+        a.x -= ci.x * cj.x + ci.y * cj.y;  // ci conj(cj)
+        a.y -= ci.y * cj.x - ci.x * cj.y;
+        A[i * ld + j] = a;
+      }
     }
-    __syncthreads();
+    g.sync();
   }
-  for (int idx = tid; idx < m * m; idx += blockDim.x) {
-    const int i = idx / m, j = idx % m;
-    if (j > i || j >= r) A[i * ld + j] = make_float2(0.f, 0.f);
-  }
+  for (int i = warp; i < m; i += nw)
+    for (int j = lane; j < m; j += 32)
+      if (j > i || j >= r) A[i * ld + j] = make_float2(0.f, 0.f);
   if (tid == 0) *rank = r;
-  __syncthreads();
+  g.sync();
 }
 
 struct Smem {
   float2* X;       // n x n: G_w -> L_w -> K^T -> rotated columns of K
-  float2* Lv;      // 2 blocks chi x chi: L_0, L_1
+  float2* Lv;      // 2 blocks chi x (chi + 1): L_0, L_1 (padded rows)
   int* perm_w;     // n
   int* perm_v;     // 2 chi
   int* src;        // n: K^T gather map
@@ -157,7 +175,7 @@ struct Smem {
   double* sig;     // n
   double* scal;    // 4
   double* red_d;   // 32
-  float2* colk;    // n
+  float2* colk;    // 2 n (one column buffer per concurrent factorisation)
   float* nrm;      // n: squared row norms during the Jacobi
 };
 
@@ -166,11 +184,11 @@ __device__ Smem carve(unsigned char* base, int chi) {
   Smem s;
   unsigned char* p = base;
   s.X = reinterpret_cast<float2*>(p); p += sizeof(float2) * n * n;
-  s.Lv = reinterpret_cast<float2*>(p); p += sizeof(float2) * 2 * chi * chi;
+  s.Lv = reinterpret_cast<float2*>(p); p += sizeof(float2) * 2 * chi * (chi + 1);
   s.sig = reinterpret_cast<double*>(p); p += sizeof(double) * n;
   s.scal = reinterpret_cast<double*>(p); p += sizeof(double) * 4;
   s.red_d = reinterpret_cast<double*>(p); p += sizeof(double) * 32;
-  s.colk = reinterpret_cast<float2*>(p); p += sizeof(float2) * n;
+  s.colk = reinterpret_cast<float2*>(p); p += sizeof(float2) * 2 * n;
   s.nrm = reinterpret_cast<float*>(p); p += sizeof(float) * n;
   s.perm_w = reinterpret_cast<int*>(p); p += sizeof(int) * n;
   s.perm_v = reinterpret_cast<int*>(p); p += sizeof(int) * 2 * chi;
@@ -197,9 +215,11 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   const float sg = (float)a.sign;
 
   // 1. Gram matrices: G_v blocks conj(N_p^v) in Lv, G_w from conj(N_q^w) in X.
+  const int ldv = chi + 1;
   for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
     const int p = idx / (chi * chi), o = idx % (chi * chi);
-    s.Lv[idx] = make_float2(gv[p * 2 * c2 + o], -gv[p * 2 * c2 + c2 + o]);
+    s.Lv[p * chi * ldv + (o / chi) * ldv + o % chi] =
+        make_float2(gv[p * 2 * c2 + o], -gv[p * 2 * c2 + c2 + o]);
   }
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx % n;
@@ -222,10 +242,18 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   __syncthreads();
   const float ctol = 1e-7f;
   float2* colk = reinterpret_cast<float2*>(s.colk);
-  pivoted_cholesky32(s.Lv, chi, chi, s.perm_v, ctol, &s.rank[0], s.red_v, s.red_i, s.dmax0, colk);
-  pivoted_cholesky32(s.Lv + chi * chi, chi, chi, s.perm_v + chi, ctol, &s.rank[1], s.red_v,
-                     s.red_i, s.dmax0, colk);
-  pivoted_cholesky32(X, n, n, s.perm_w, ctol, &s.rank[2], s.red_v, s.red_i, s.dmax0, colk);
+  {
+    // the two v-side blocks concurrently on the two halves of the block, then G_w
+    const int half_t = kThreads / 2;
+    const int h = tid >= half_t;
+    const Group gh{h * half_t, half_t, 1 + h};
+    pivoted_cholesky32(s.Lv + h * chi * ldv, chi, ldv, s.perm_v + h * chi, ctol, &s.rank[h],
+                       s.red_i + h, s.red_v + h, s.dmax0 + h, colk + h * n, gh);
+    __syncthreads();
+    const Group gall{0, kThreads, 0};
+    pivoted_cholesky32(X, n, n, s.perm_w, ctol, &s.rank[2], s.red_i, s.red_v, s.dmax0 + 2, colk,
+                       gall);
+  }
 
   // 2. K^T = R_w R_v^T.  First X <- conj(L_w^T) so that row j of X holds
   //    R_w[j][perm_w[t]] at column t.  Then with c = perm_b[t'] (block b):
@@ -252,6 +280,52 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   for (int bt = tid; bt < n; bt += blockDim.x) s.src[bt] = s.order[bt];
   __syncthreads();
   const int npl = n / 32 > 0 ? (n + 31) / 32 : 1;  // values per lane (<= 4)
+  if (n % 32 == 0) {
+    // Each warp owns n/32 whole rows j, each lane n/32 consecutive output
+    // columns o = (b, i) (all in one block b): a register tile of rows x
+    // columns over t', the rows' gathered values broadcast from shared memory,
+    // the lane's L_b row segment read contiguously.  Rows are written back in
+    // place once the warp has read them.
+    const int cl = n / 32;            // columns per lane, rows per warp
+    const int o0 = lane * cl;
+    const int b = o0 / chi, i0 = o0 - b * chi;
+    const float2* Lb = s.Lv + b * chi * ldv;
+    const int* srcb = s.src + b * chi;
+    for (int r0 = 0; r0 < cl; r0 += 2) {
+      const int j0 = warp * cl + r0;
+      const int nr = cl - r0 < 2 ? cl - r0 : 2;
+      float2 acc[2][4];
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+      for (int tp = 0; tp < chi; ++tp) {
+        const int col = srcb[tp];
+        float2 y[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) y[r] = r < nr ? X[(j0 + r) * n + col] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c < cl) {
+            const float2 z = cconjf(Lb[tp * ldv + i0 + c]);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const float2 pz = cmulf(y[r], z);
+              acc[r][c].x += pz.x;
+              acc[r][c].y += pz.y;
+            }
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (r < nr && c < cl) X[(j0 + r) * n + o0 + c] = acc[r][c];
+      __syncwarp();
+    }
+  } else {
   for (int j = warp; j < n; j += kWarps) {
     float2 y[4];
 #pragma unroll
@@ -265,14 +339,14 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     for (int bt = 0; bt < n; ++bt) {
       const float2 yv = shfl2(y[bt >> 5], bt & 31);
       const int b = bt / chi, tp = bt % chi;
-      const float2* Lb = s.Lv + b * chi * chi;
+      const float2* Lb = s.Lv + b * chi * ldv;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int o = u * 32 + lane;  // output (b, i) = o
         if (u < npl && o < n && o / chi == b) {
           const int i = o % chi;
           if (i <= tp) {
-            const float2 p = cmulf(yv, cconjf(Lb[tp * chi + i]));
+            const float2 p = cmulf(yv, cconjf(Lb[tp * ldv + i]));
             out[u].x += p.x;
             out[u].y += p.y;
           }
@@ -285,6 +359,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
       const int o = u * 32 + lane;
       if (u < npl && o < n) X[j * n + o] = out[u];
     }
+  }
   }
   __syncthreads();
 
@@ -514,7 +589,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     const float fw = keep ? (float)(1.0 / sqrt(sgm * nrm)) : 0.f;  // 1/sqrt(sigma ||sigma||)
     const float inv_s = keep ? (float)(1.0 / sgm) : 0.f;
     for (int b = 0; b < 2; ++b) {
-      const float2* Lb = s.Lv + b * chi * chi;
+      const float2* Lb = s.Lv + b * chi * ldv;
       const int rb = s.rank[b];
       const int* pb = s.perm_v + b * chi;
       // u block b, lane owns entries i = lane, lane + 32
@@ -526,27 +601,26 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
         u[h].x *= inv_s;
         u[h].y *= inv_s;
       }
-      // C_v block b: solve L_b^H w = u (back substitution over t < rank), z[perm[t]] = w[t]
+      // C_v block b: solve L_b^H w = u by columns (t < rank, from the last):
+      // w[t] = u[t] / L[t][t], then u[t'] -= conj(L[t][t']) w[t] for t' < t
+      // (row t of L, contiguous over the lanes), z[perm[t]] = w[t]
       float2 w[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      float2 uu[2] = {u[0], u[1]};
       for (int t = rb - 1; t >= 0; --t) {
-        // w[t] = (u[t] - sum_{t2 > t} conj(L[t2][t]) w[t2]) / L[t][t]
-        float2 part = make_float2(0.f, 0.f);
+        const float2 ut = shfl2(uu[t >> 5], t & 31);
+        const float d = Lb[t * ldv + t].x;
+        const float2 wt = make_float2(ut.x / d, ut.y / d);
+        if ((t >> 5) == 0 && lane == (t & 31)) w[0] = wt;
+        if ((t >> 5) == 1 && lane == (t & 31)) w[1] = wt;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int t2 = h * 32 + lane;
-          if (t2 > t && t2 < rb) {
-            const float2 pr = cmulf(cconjf(Lb[t2 * chi + t]), w[h]);
-            part.x += pr.x;
-            part.y += pr.y;
+          if (t2 < t) {
+            const float2 pr = cmulf(cconjf(Lb[t * ldv + t2]), wt);
+            uu[h].x -= pr.x;
+            uu[h].y -= pr.y;
           }
         }
-        part.x = warp_sum(part.x);
-        part.y = warp_sum(part.y);
-        const float2 ut = shfl2(u[t >> 5], t & 31);
-        const float d = Lb[t * chi + t].x;
-        const float2 wt = make_float2((ut.x - part.x) / d, (ut.y - part.y) / d);
-        if ((t >> 5) == 0 && lane == (t & 31)) w[0] = wt;
-        if ((t >> 5) == 1 && lane == (t & 31)) w[1] = wt;
       }
       // D_v[p = b][e][m] = z[e] * sqrt(S_m), e = perm_b[t]
 #pragma unroll
@@ -568,7 +642,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
         for (int h = 0; h < 2; ++h) {
           const int t = h * 32 + lane;
           if (t < chi && i <= t) {
-            const float2 pr = cmulf(Lb[t * chi + i], ui);
+            const float2 pr = cmulf(Lb[t * ldv + i], ui);
             y[h].x += pr.x;
             y[h].y += pr.y;
           }
@@ -618,8 +692,8 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
 
 size_t smem_bytes(int chi) {
   const int n = 2 * chi;
-  return sizeof(float2) * (size_t)n * n + sizeof(float2) * 2 * chi * chi + sizeof(double) * (n + 4 + 32) +
-         sizeof(double) * 2 * n +
+  return sizeof(float2) * (size_t)n * n + sizeof(float2) * 2 * chi * (chi + 1) +
+         sizeof(double) * (n + 4 + 32) + sizeof(double) * 2 * n + sizeof(float2) * n +
          sizeof(int) * (n + 2 * chi + n + n + 4 + 32) + sizeof(float) * (32 + 4) + sizeof(int) * 4 +
          sizeof(float) * n + 64;
 }
