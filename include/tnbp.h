@@ -149,6 +149,7 @@ typedef struct {
   int64_t tma_launches;      /* of which launches of the TMA-fed streaming kernel */
   int64_t solve_edges;       /* truncation solves (gate edges) of the call */
   int64_t solve_sweeps;      /* Jacobi rotation sweeps summed over those solves */
+  int64_t solve_sweeps_max;  /* the largest count of one solve */
 } tn_stats;
 
 /*

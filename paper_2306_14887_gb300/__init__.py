@@ -66,7 +66,8 @@ class tn_stats(C.Structure):
                 ("bp_iters_total", C.c_int32), ("bp_residual_last", C.c_double),
                 ("discarded_max", C.c_double), ("discarded_sum", C.c_double),
                 ("kernel_launches", C.c_int64), ("tma_launches", C.c_int64),
-                ("solve_edges", C.c_int64), ("solve_sweeps", C.c_int64)]
+                ("solve_edges", C.c_int64), ("solve_sweeps", C.c_int64),
+                ("solve_sweeps_max", C.c_int64)]
 
 
 class tn_profile(C.Structure):

@@ -887,6 +887,7 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
     const double dw = h->h_stats[4 * i];
     h->stats.solve_edges++;
     h->stats.solve_sweeps += (int64_t)h->h_stats[4 * i + 3];
+    h->stats.solve_sweeps_max = std::max(h->stats.solve_sweeps_max, (int64_t)h->h_stats[4 * i + 3]);
     h->stats.discarded_sum += dw;
     h->stats.discarded_max = std::max(h->stats.discarded_max, dw);
   }

@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   }
   const float abs_floor = (float)(kAbsTol * s.scal[2]);
   const float orth_tol = a.orth_tol > 0.f ? a.orth_tol : 2e-6f;
+  const float orth_tol2 = orth_tol * orth_tol, abs_floor2 = abs_floor * abs_floor;
   const int half = n / 2;
   int sweeps = 0;
   if (n % 32 == 0) {
@@ -437,15 +438,33 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
             gi += __shfl_xor_sync(0xffffffffu, gi, o);
           }
           const float al = s.nrm[p], be = s.nrm[q];
-          const float gm = sqrtf(gr * gr + gi * gi);
-          if (gm > orth_tol * sqrtf(al * be) && gm > abs_floor && gm > 0.f) {
-            const float igm = 1.f / gm;
-            const float2 ph = make_float2(gr * igm, -gi * igm);  // e^{-i phi}
-            const float tau = (be - al) * 0.5f * igm;
-            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            // exactly rounded: an approximate reciprocal square root makes every
-            // rotation slightly non-unitary and the row norms drift
-            const float cs = 1.f / sqrtf(1.f + t * t);
+          const float g2 = gr * gr + gi * gi;
+          // |gamma| > orth_tol sqrt(al be) and |gamma| > abs_floor, compared squared
+          if (g2 > orth_tol2 * al * be && g2 > abs_floor2 && g2 > 0.f) {
+            // 1/|gamma| and cos = 1/sqrt(1 + t^2) from the hardware reciprocal
+            // square root refined by one step of Newton's iteration
+            // y <- y (3 - x y^2) / 2: the phase e^{-i phi} and the pair (cos, sin)
+            // are then unit to about one ulp, so the rotations stay unitary and
+            // the row norms do not drift.  t itself may be approximate: any t
+            // gives a unitary rotation, and an inexact angle only leaves a
+            // residual overlap that later rounds remove.
+            float ig = rsqrtf(g2);
+            ig = ig * (1.5f - 0.5f * g2 * ig * ig);
+            const float gm = g2 * ig;
+            const float2 ph = make_float2(gr * ig, -gi * ig);  // e^{-i phi}
+            const float tau = (be - al) * 0.5f * ig;
+            const float at = fabsf(tau);
+            float t;
+            if (at < 1e15f) {
+              const float q1 = 1.f + at * at;
+              t = __fdividef(1.f, at + q1 * rsqrtf(q1));  // 1 / (|tau| + sqrt(1 + tau^2))
+            } else {
+              t = 0.5f / at;
+            }
+            if (tau < 0.f) t = -t;
+            const float q2 = 1.f + t * t;
+            float cs = rsqrtf(q2);
+            cs = cs * (1.5f - 0.5f * q2 * cs * cs);
             const float sn = t * cs;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
