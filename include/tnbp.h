@@ -76,9 +76,18 @@ typedef struct {
   int32_t periodic;
 } tn_graph;
 
-/* Arithmetic of the message and gate contractions.  FP64 is used for the
- * truncation solve and for the BP convergence and normalisation reductions
- * in every mode.  TN_FP32: plain FP32 on the CUDA cores. */
+/* Arithmetic of the message and gate contractions (tensor-core modes
+ * accumulate in FP32 in tensor memory).  FP64 is used for the BP convergence
+ * and normalisation reductions in every mode and for the truncation solve's
+ * spectrum.
+ *   TN_FP32    plain FP32 on the CUDA cores.
+ *   TN_TF32    TF32 operands (10-bit mantissa).
+ *   TN_BF16    BF16 operands (7-bit mantissa).
+ *   TN_BF16X3, TN_TF32X3  split-precision products: each operand is x = hi + lo
+ *              with hi = round(x), lo = round(x - hi) in the operand format, and
+ *              the product is accumulated as hi*hi + hi*lo + lo*hi (three
+ *              tensor-core products; the dropped lo*lo term is below FP32
+ *              rounding for TF32X3, about 2^-16 relative for BF16X3). */
 typedef enum {
   TN_FP32 = 0,
   TN_TF32 = 1,

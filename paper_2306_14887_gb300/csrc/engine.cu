@@ -391,7 +391,7 @@ void gemm_work(const GemmDesc& d, double* flops, double* bytes) {
 }
 
 bool use_tensor_cores(const tn_handle* h) {
-  return h->cfg.prec == TN_TF32 || h->cfg.prec == TN_BF16;
+  return h->cfg.prec != TN_FP32;
 }
 
 tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
@@ -805,6 +805,7 @@ double solve_tol(const tn_handle* h) {
   if (h->cfg.solve_tol > 0) return h->cfg.solve_tol;
   if (h->cfg.prec == TN_TF32) return 1e-4;
   if (h->cfg.prec == TN_BF16) return 1e-3;
+  if (h->cfg.prec == TN_BF16X3) return 1e-5;
   return 2e-6;
 }
 
@@ -826,7 +827,8 @@ double precision_floor(const tn_handle* h) {
   switch (h->cfg.prec) {
     case TN_TF32: return 2e-3;
     case TN_BF16: return 2e-2;
-    default: return 2e-6;
+    case TN_BF16X3: return 2e-5;  // split BF16: about 16 significant bits per operand
+    default: return 2e-6;         // FP32 and split TF32 (about 21 bits)
   }
 }
 
@@ -1139,10 +1141,7 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   *out = nullptr;
   if (cfg->chi < 1 || cfg->chi > 256) { set_error("chi must be in 1..256"); return TN_EINVAL; }
   if (cfg->prec < TN_FP32 || cfg->prec > TN_TF32X3) { set_error("unknown precision"); return TN_EINVAL; }
-  if (cfg->prec != TN_FP32 && cfg->prec != TN_TF32 && cfg->prec != TN_BF16) {
-    set_error("precision mode not built yet");
-    return TN_EUNSUPPORTED;
-  }
+
   if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64) {
     set_error("unknown truncation solve");
     return TN_EINVAL;

@@ -48,8 +48,10 @@ constexpr int kBatch = 8;                        // 16-byte loads in flight per 
 struct TcSmem {
   static constexpr int kA = kTM * kRowBytes;   // 16 KB per stage
   static constexpr int kB = kTN * kRowBytes;   // 16 KB per stage
-  static constexpr int kBarOff = kStages * (kA + kB);
-  static constexpr int kBytes = kBarOff + 128;
+  // the hi tiles of every stage; with split precision the lo tiles follow
+  static constexpr int kHi = kStages * (kA + kB);
+  __host__ __device__ static constexpr int bar_off(int x3) { return kHi * (x3 ? 2 : 1); }
+  __host__ __device__ static constexpr int bytes(int x3) { return bar_off(x3) + 128; }
 };
 
 __device__ __forceinline__ int64_t koff(int k, int K2, int64_t s1, int64_t s2) {
@@ -60,6 +62,7 @@ __device__ __forceinline__ int64_t koff(int k, int K2, int64_t s1, int64_t s2) {
 struct TcArgs {
   int quad;        // 0: REAL_B, 1: QUAD
   int bf16;        // operand format: 0 TF32, 1 BF16
+  int x3;          // split precision: x = hi + lo, D += A_hi B_hi + A_hi B_lo + A_lo B_hi
   int mr, nr, kr;  // real GEMM sizes
   int tn;          // N tile (multiple of 16, <= 128)
   int splits;      // K splits (QUAD only)
@@ -117,6 +120,15 @@ __device__ __forceinline__ void store_k4(unsigned char* tile, int row, int kk, f
   }
 }
 
+// The part of v that the operand format does not hold: v - round(v).
+__device__ __forceinline__ float lo_part(float v, int bf16) {
+  const float hi = bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : __uint_as_float(to_tf32(v));
+  return v - hi;
+}
+__device__ __forceinline__ float4 lo_part4(float4 v, int bf16) {
+  return make_float4(lo_part(v.x, bf16), lo_part(v.y, bf16), lo_part(v.z, bf16), lo_part(v.w, bf16));
+}
+
 __device__ __forceinline__ void store_elem(unsigned char* tile, int row, int kk, float v, int bf16) {
   if (bf16) {
     // 64 bf16 per 128-byte row; 16-byte chunk = 8 elements
@@ -137,7 +149,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sA = smem;
   unsigned char* sB = smem + kStages * TcSmem::kA;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TcSmem::kBarOff);
+  unsigned char* sAl = smem + TcSmem::kHi;  // lo tiles (split precision only)
+  unsigned char* sBl = sAl + kStages * TcSmem::kA;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TcSmem::bar_off(t.x3));
   uint64_t* empty = full + kStages;
   uint64_t* accum = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
@@ -205,9 +219,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
                         (t.tn % 4 == 0) && (n0 % 4 == 0);
     const bool a_kfast = d.a_k2 == 1 && !(d.M2 > 1 && d.M3 <= 1 && d.a_m2 == 1) &&
                          !(d.M3 > 1 && d.a_m3 == 1);
-    const bool a_async = !t.bf16 && a_kvec && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+    const bool a_async = !t.bf16 && !t.x3 && a_kvec && ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                          !(d.conj_a && !t.quad);
-    const bool b_async = !t.bf16 && b_kvec && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+    const bool b_async = !t.bf16 && !t.x3 && b_kvec && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
     const bool b_nfast = d.b_n == 1;
     const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
     for (int kt = 0; kt < ntiles; ++kt) {
@@ -217,6 +231,8 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
       if (*abort_flag) { mbar_arrive(&full[s]); continue; }
       unsigned char* ta = sA + s * TcSmem::kA;
       unsigned char* tb = sB + s * TcSmem::kB;
+      unsigned char* tal = sAl + s * TcSmem::kA;
+      unsigned char* tbl = sBl + s * TcSmem::kB;
       const int k0 = kbeg + kt * kelems;
       // TF32 operands whose K index is contiguous are copied with cp.async
       // straight into their swizzled place (the tensor core reads the FP32 bits
@@ -268,7 +284,11 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             const int c = base + u * 128 + pt;
-            if (c < total) store_k4(ta, c / qpr, (c - (c / qpr) * qpr) * 4, v[u], t.bf16);
+            if (c < total) {
+              const int row = c / qpr, kk = (c - (c / qpr) * qpr) * 4;
+              store_k4(ta, row, kk, v[u], t.bf16);
+              if (t.x3) store_k4(tal, row, kk, lo_part4(v[u], t.bf16), t.bf16);
+            }
           }
         }
       } else if (a_mvec && aligned) {
@@ -302,6 +322,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
             store_elem(ta, row + 1, kk, v[u].y, t.bf16);
             store_elem(ta, row + 2, kk, v[u].z, t.bf16);
             store_elem(ta, row + 3, kk, v[u].w, t.bf16);
+            if (t.x3) {
+              const float4 l = lo_part4(v[u], t.bf16);
+              store_elem(tal, row, kk, l.x, t.bf16);
+              store_elem(tal, row + 1, kk, l.y, t.bf16);
+              store_elem(tal, row + 2, kk, l.z, t.bf16);
+              store_elem(tal, row + 3, kk, l.w, t.bf16);
+            }
           }
         }
       } else {
@@ -312,6 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
           const int mr = m0 + row, kr = k0 + kk;
           const float v = (mr < t.mr && kr < kend) ? load_a(d, t, A, mr, kr) : 0.f;
           store_elem(ta, row, kk, v, t.bf16);
+          if (t.x3) store_elem(tal, row, kk, lo_part(v, t.bf16), t.bf16);
         }
       }
       if (b_async) {
@@ -350,7 +378,11 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             const int c = base + u * 128 + pt;
-            if (c < total) store_k4(tb, c / qpr, (c - (c / qpr) * qpr) * 4, v[u], t.bf16);
+            if (c < total) {
+              const int row = c / qpr, kk = (c - (c / qpr) * qpr) * 4;
+              store_k4(tb, row, kk, v[u], t.bf16);
+              if (t.x3) store_k4(tbl, row, kk, lo_part4(v[u], t.bf16), t.bf16);
+            }
           }
         }
       } else if (b_nvec && aligned) {
@@ -389,6 +421,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
             store_elem(tb, row + 1, kk, v[u].y, t.bf16);
             store_elem(tb, row + 2, kk, v[u].z, t.bf16);
             store_elem(tb, row + 3, kk, v[u].w, t.bf16);
+            if (t.x3) {
+              const float4 l = lo_part4(v[u], t.bf16);
+              store_elem(tbl, row, kk, l.x, t.bf16);
+              store_elem(tbl, row + 1, kk, l.y, t.bf16);
+              store_elem(tbl, row + 2, kk, l.z, t.bf16);
+              store_elem(tbl, row + 3, kk, l.w, t.bf16);
+            }
           }
         }
       } else {
@@ -399,6 +438,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
           const int nr = n0 + row, kr = k0 + kk;
           const float v = (nr < t.nr && kr < kend) ? load_b(d, t, B, nr, kr) : 0.f;
           store_elem(tb, row, kk, v, t.bf16);
+          if (t.x3) store_elem(tbl, row, kk, lo_part(v, t.bf16), t.bf16);
         }
       }
       if (!(a_async && b_async)) fence_proxy_async();  // generic-proxy stores of this stage
@@ -420,10 +460,17 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
           tc_fence_after();
           const uint32_t a0 = smem_u32(sA + s * TcSmem::kA);
           const uint32_t b0 = smem_u32(sB + s * TcSmem::kB);
+          const uint32_t al = smem_u32(sAl + s * TcSmem::kA);
+          const uint32_t bl = smem_u32(sBl + s * TcSmem::kB);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)  // 4 x 32 bytes of K per 128-byte row
+          for (int ks = 0; ks < 4; ++ks) {  // 4 x 32 bytes of K per 128-byte row
             mma_issue(t.bf16, tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
                       (kt > 0 || ks > 0) ? 1u : 0u);
+            if (t.x3) {
+              mma_issue(t.bf16, tmem, sw128_desc(a0 + ks * 32), sw128_desc(bl + ks * 32), idesc, 1u);
+              mma_issue(t.bf16, tmem, sw128_desc(al + ks * 32), sw128_desc(b0 + ks * 32), idesc, 1u);
+            }
+          }
         }
         mma_commit(&empty[s]);
       }
@@ -536,7 +583,7 @@ __global__ void tc_reduce_kernel(GemmDesc d, const float* part, int splits) {
 
 }  // namespace
 
-size_t tc_smem_bytes() { return TcSmem::kBytes + 1024; }
+size_t tc_smem_bytes(int x3) { return TcSmem::bytes(x3) + 1024; }
 
 // Sum split-K partials [split][outer][inner][re|im][M][N] into C in a fixed order.
 cudaError_t launch_tc_reduce(const GemmDesc& d, const float* part, int splits, cudaStream_t st) {
@@ -569,7 +616,7 @@ cudaError_t tc_prepare() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_smem_bytes());
+                                       (int)tc_smem_bytes(1));
   if (e != cudaSuccess) return e;
   // two CTAs per SM: ask for the largest shared-memory carveout
   e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -588,7 +635,8 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
   if (splits > 1 && !part) return cudaErrorInvalidValue;
   TcArgs t;
   t.quad = quad;
-  t.bf16 = (d.prec == TN_BF16) ? 1 : 0;
+  t.bf16 = (d.prec == TN_BF16 || d.prec == TN_BF16X3) ? 1 : 0;
+  t.x3 = (d.prec == TN_TF32X3 || d.prec == TN_BF16X3) ? 1 : 0;
   const int64_t K = (int64_t)d.K1 * d.K2;
   if (quad) { t.mr = 2 * d.M; t.nr = 2 * d.N; t.kr = (int)K; }
   else { t.mr = d.M; t.nr = 2 * d.N; t.kr = (int)(2 * K); }
@@ -604,7 +652,7 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
     if (e != cudaSuccess) return e;
   }
   dim3 grid((t.nr + t.tn - 1) / t.tn, (t.mr + kTM - 1) / kTM, d.n_outer * d.n_inner * splits);
-  tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(), st>>>(d, t);
+  tc_gemm_kernel<<<grid, kThreads, tc_smem_bytes(t.x3), st>>>(d, t);
   if (n_kernels) *n_kernels = splits > 1 ? 2 : 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
