@@ -179,8 +179,9 @@ tn_status tn_destroy(tn_handle* h);
  * = exp(-i theta_h X/2) on every site, then exp(+i pi/4 Z_v Z_w) on every edge
  * by the BP-gauged simple update (Methods, "The simple update procedure": the
  * environment of each tensor is the product of its incoming messages; the
- * two-site bond is truncated to the chi largest singular values by an FP64
- * solve; the messages on the gate edge become diag(S) with ||S||_2 = 1), colour
+ * two-site bond is truncated to the chi largest singular values by the
+ * truncation solve of tn_config; the messages on the gate edge become diag(S)
+ * with ||S||_2 = 1), colour
  * layer by colour layer, then BP regauging with the handle's bp_tol and
  * bp_max_iters ("State ansatz": regauge after every Trotter step).
  * theta_h may be any real.  steps >= 0.
@@ -188,6 +189,17 @@ tn_status tn_destroy(tn_handle* h);
  * evolution still completed), TN_ECUDA.
  */
 tn_status tn_apply_floquet(tn_handle* h, double theta_h, int32_t steps);
+
+/*
+ * tn_apply_floquet_field — tn_apply_floquet with a kick angle per vertex:
+ * RX(theta_v[v]) on site v.  theta_v: n_vertices host doubles (caller-owned,
+ * copied at the call).  Used to evolve many independent instances as one
+ * graph (their disjoint union): BP and the gates never couple components, so
+ * each component evolves as it would alone, while every contraction of every
+ * instance runs in the same launches.  Errors: as tn_apply_floquet, plus
+ * TN_EINVAL for a null or non-finite theta_v.
+ */
+tn_status tn_apply_floquet_field(tn_handle* h, const double* theta_v, int32_t steps);
 
 /*
  * tn_apply_clifford_dagger — apply U(pi/2)^dagger `steps` times: the ZZ layers
@@ -316,6 +328,63 @@ tn_status tn_footprint(const tn_handle* h, size_t* bytes_out);
 /* Footprint tn_create would need for this graph and config (admission). */
 tn_status tn_footprint_estimate(const tn_graph* graph, const tn_config* cfg,
                                 size_t* bytes_out);
+
+/*
+ * Serving (continuous batching).  A server runs (graph, chi, theta_h, steps)
+ * jobs as they arrive: max_slots host threads, each driving one job at a time
+ * on its own CUDA stream, so that concurrent jobs' kernels overlap on the
+ * device.  A queued job is admitted (oldest first) once the sum of the
+ * resident jobs' footprints (tn_footprint_estimate: state, messages,
+ * workspaces) plus its own fits the HBM budget.  A job's device memory is
+ * allocated stream-ordered on its slot's stream and released when it ends.
+ * Its result, <Z_v> for every vertex after the last step, does not depend on
+ * what else runs (no shared buffers; deterministic kernels).
+ */
+typedef struct tn_server tn_server;
+
+typedef struct {
+  size_t hbm_budget;   /* bytes the resident jobs may hold; 0: 90% of free device memory */
+  int32_t max_slots;   /* jobs resident and running at once, 1..64 */
+  int32_t device;      /* CUDA device ordinal */
+} tn_server_config;
+
+typedef struct {
+  tn_graph graph;      /* copied at submit */
+  tn_config cfg;       /* chi, precision, tolerances as for tn_create */
+  double theta_h;
+  int32_t steps;
+} tn_job;
+
+typedef struct {
+  int32_t status;      /* the job's status: TN_OK, TN_ENOTCONVERGED, or an error */
+  int32_t n_vertices;
+  int32_t steps_done;
+  double queue_s;      /* submit to admission, seconds */
+  double latency_s;    /* submit to result, seconds */
+} tn_result;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int32_t resident, peak_resident, queued;
+  size_t used_bytes, peak_bytes, budget_bytes;
+} tn_server_stats;
+
+/* tn_server_create — start the slots.  Errors: TN_EINVAL (max_slots outside
+ * 1..64, negative device), TN_ECUDA (no such device). */
+tn_status tn_server_create(const tn_server_config* cfg, tn_server** out);
+/* tn_server_submit — queue a job; *ticket identifies it.  Errors: TN_EINVAL
+ * (graph or config), TN_ENOMEM (its footprint alone exceeds the budget). */
+tn_status tn_server_submit(tn_server* s, const tn_job* job, uint64_t* ticket);
+/* tn_server_poll — TN_EAGAIN while the job is queued or running; otherwise the
+ * job's status, with z (caller-owned, n_vertices doubles, may be NULL) and info
+ * (may be NULL) filled; the ticket is then released.  TN_EINVAL: unknown ticket. */
+tn_status tn_server_poll(tn_server* s, uint64_t ticket, double* z, tn_result* info);
+/* tn_server_wait — tn_server_poll after waiting up to timeout_s seconds. */
+tn_status tn_server_wait(tn_server* s, uint64_t ticket, double timeout_s, double* z,
+                         tn_result* info);
+tn_status tn_server_get_stats(tn_server* s, tn_server_stats* out);
+/* tn_server_destroy — drop queued jobs, wait for the resident ones, join the slots. */
+tn_status tn_server_destroy(tn_server* s);
 
 /*
  * tn_heavy_hex — the heavy-hex patch with `rows` rows (odd) of `cols` columns

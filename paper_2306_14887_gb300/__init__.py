@@ -31,7 +31,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_footprint_estimate", "tn_heavy_hex", "tn_clifford_reduce", "tn_profile_enable",
            "tn_profile_read", "tn_profile_class_name", "tn_truncation_solve",
            "tn_truncation_solve_noalloc", "tn_truncation_solve_ex", "tn_last_error",
-           "tn_version"]
+           "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
+           "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy"]
 
 
 class TNError(RuntimeError):
@@ -80,6 +81,27 @@ class tn_pauli(C.Structure):
                 ("paulis", C.c_char_p), ("sign", C.c_int8)]
 
 
+class tn_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int32), ("device", C.c_int32)]
+
+
+class tn_job(C.Structure):
+    _fields_ = [("graph", tn_graph), ("cfg", tn_config), ("theta_h", C.c_double),
+                ("steps", C.c_int32)]
+
+
+class tn_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_vertices", C.c_int32), ("steps_done", C.c_int32),
+                ("queue_s", C.c_double), ("latency_s", C.c_double)]
+
+
+class tn_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("resident", C.c_int32), ("peak_resident", C.c_int32), ("queued", C.c_int32),
+                ("used_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("budget_bytes", C.c_size_t)]
+
+
 _lib = None
 
 
@@ -119,6 +141,13 @@ def lib():
         L.tn_truncation_solve.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
         L.tn_truncation_solve_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
         L.tn_truncation_solve_ex.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, i32, vp]
+        L.tn_apply_floquet_field.argtypes = [vp, dp, i32]
+        L.tn_server_create.argtypes = [C.POINTER(tn_server_config), C.POINTER(vp)]
+        L.tn_server_submit.argtypes = [vp, C.POINTER(tn_job), C.POINTER(C.c_uint64)]
+        L.tn_server_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(tn_result)]
+        L.tn_server_wait.argtypes = [vp, C.c_uint64, C.c_double, dp, C.POINTER(tn_result)]
+        L.tn_server_get_stats.argtypes = [vp, C.POINTER(tn_server_stats)]
+        L.tn_server_destroy.argtypes = [vp]
         L.tn_last_error.restype = C.c_char_p
         L.tn_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -283,6 +312,17 @@ class TNState:
             _check(s)
         return s
 
+    def apply_floquet_field(self, thetas, steps, check=True):
+        """U with a kick angle per vertex (thetas: n values)."""
+        th = np.ascontiguousarray(thetas, dtype=np.float64).reshape(-1)
+        if th.size != self.n:
+            raise ValueError(f"need {self.n} angles, got {th.size}")
+        s = lib().tn_apply_floquet_field(self._h, th.ctypes.data_as(C.POINTER(C.c_double)),
+                                         int(steps))
+        if check and s not in (TN_OK, -3):
+            _check(s)
+        return s
+
     def apply_clifford_dagger(self, steps):
         s = lib().tn_apply_clifford_dagger(self._h, int(steps))
         if s not in (TN_OK, -3):
@@ -374,6 +414,92 @@ class TNState:
         buf[0::2], buf[1::2] = m.real, m.imag
         _check(lib().tn_set_message(self._h, int(e), int(src),
                                     buf.ctypes.data_as(C.POINTER(C.c_float)), buf.size))
+
+
+def batch_union(instances):
+    """Disjoint union of graphs [(n, edges, colours), ...] -> (n, edges, colours,
+    offsets): instance i's vertex v is vertex offsets[i] + v of the union.  Many
+    instances evolve as one handle (one set of launches per contraction) with
+    TNState.apply_floquet_field carrying each instance's kick angle."""
+    offs, es, cs = [], [], []
+    n = 0
+    for (ni, ei, ci) in instances:
+        offs.append(n)
+        e = np.asarray(ei, dtype=np.int32).reshape(-1, 2)
+        es.append(e + n)
+        cs.append(np.asarray(ci, dtype=np.uint8).reshape(-1))
+        n += int(ni)
+    return n, np.concatenate(es), np.concatenate(cs), offs
+
+
+class Server:
+    """Continuous-batching job server on one device (see tn_server_* in tnbp.h)."""
+
+    def __init__(self, slots=4, hbm_budget=0, device=None):
+        import torch
+        cfg = tn_server_config()
+        cfg.hbm_budget = int(hbm_budget)
+        cfg.max_slots = int(slots)
+        cfg.device = int(torch.cuda.current_device() if device is None else device)
+        h = C.c_void_p()
+        _check(lib().tn_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def submit(self, n, edges, colours, chi, theta, steps, prec="fp32", bp_tol=1e-10,
+               bp_max_iters=1000, svd_cutoff=0.0, solve="auto"):
+        g, keep = _graph_struct(n, edges, colours)
+        job = tn_job()
+        job.graph = g
+        job.cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve)
+        job.theta_h = float(theta)
+        job.steps = int(steps)
+        t = C.c_uint64()
+        _check(lib().tn_server_submit(self._h, C.byref(job), C.byref(t)))
+        del keep
+        self._n[t.value] = int(n)
+        return t.value
+
+    def _take(self, fn, ticket, *extra):
+        z = np.zeros(self._n[ticket], dtype=np.float64)
+        info = tn_result()
+        st = fn(self._h, C.c_uint64(ticket), *extra,
+                z.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info))
+        if st == -7:  # TN_EAGAIN
+            return None
+        del self._n[ticket]
+        _check(st if st != -3 else 0)
+        return z, {"status": info.status, "steps_done": info.steps_done,
+                   "queue_s": info.queue_s, "latency_s": info.latency_s}
+
+    def poll(self, ticket):
+        """None while queued or running, else (<Z_v> array, info dict)."""
+        return self._take(lib().tn_server_poll, ticket)
+
+    def wait(self, ticket, timeout=600.0):
+        return self._take(lib().tn_server_wait, ticket, C.c_double(timeout))
+
+    def stats(self):
+        s = tn_server_stats()
+        _check(lib().tn_server_get_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in tn_server_stats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().tn_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def version():

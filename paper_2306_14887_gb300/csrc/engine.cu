@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <string>
 #include <vector>
@@ -102,6 +103,8 @@ struct tn_handle {
   int* flags = nullptr;
   double* rho = nullptr;
   int64_t* site_offs_by_deg[4] = {nullptr, nullptr, nullptr, nullptr};
+  float2* rx_cs = nullptr;   // per-site (cos, sin) of theta_v / 2, by degree blocks
+  int rx_base[4] = {0, 0, 0, 0};
   int n_by_deg[4] = {0, 0, 0, 0};
   std::vector<int> sites_by_deg[4];
 
@@ -792,6 +795,35 @@ tn_status phys_gate(tn_handle* h, const double u[8]) {
   return TN_OK;
 }
 
+// RX(theta_v) with a per-site angle: (cos, sin) of theta_v / 2 uploaded once
+// per call, then one launch per degree each step.
+tn_status upload_rx_field(tn_handle* h, const double* theta_v) {
+  std::vector<float2> cs(h->g.n);
+  for (int d = 1; d <= 3; ++d)
+    for (int i = 0; i < h->n_by_deg[d]; ++i) {
+      const double th = theta_v[h->sites_by_deg[d][i]];
+      cs[h->rx_base[d] + i] = make_float2((float)cos(th / 2), (float)sin(th / 2));
+    }
+  TN_CUDA_TRY(cudaMemcpyAsync(h->rx_cs, cs.data(), sizeof(float2) * cs.size(),
+                              cudaMemcpyHostToDevice, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status phys_gate_field(tn_handle* h) {
+  h->ta_valid = false;
+  for (int d = 1; d <= 3; ++d) {
+    if (!h->n_by_deg[d]) continue;
+    const int64_t len = ipow(h->chi, d);
+    const int pi = prof_begin(h, P_PHYS);
+    TN_CUDA_TRY(launch_phys_gate_field(h->T, h->site_offs_by_deg[d], h->rx_cs + h->rx_base[d],
+                                       h->n_by_deg[d], len, 2 * len, h->stream));
+    prof_end(h, pi, 16.0 * len * h->n_by_deg[d], 2.0 * 16.0 * len * h->n_by_deg[d]);
+    h->stats.kernel_launches++;
+  }
+  return TN_OK;
+}
+
 void rx_matrix(double theta, double u[8]) {
   const double c = cos(theta / 2), s = sin(theta / 2);
   // [[c, -i s], [-i s, c]]
@@ -1220,10 +1252,13 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->res_bits = (unsigned long long*)dev_alloc(h, 64);
   h->flags = h->res_bits ? reinterpret_cast<int*>(h->res_bits + 1) : nullptr;
   h->rho = (double*)dev_alloc(h, sizeof(double) * 8 * g.n);
-  for (int d = 1; d <= 3; ++d) {
+  for (int d = 1, base = 0; d <= 3; ++d) {
     h->n_by_deg[d] = (int)h->sites_by_deg[d].size();
     h->site_offs_by_deg[d] = (int64_t*)dev_alloc(h, sizeof(int64_t) * (h->n_by_deg[d] + 1));
+    h->rx_base[d] = base;
+    base += h->n_by_deg[d];
   }
+  h->rx_cs = (float2*)dev_alloc(h, sizeof(float2) * std::max(1, g.n));
   const int nl = (int)g.layers.size();
   h->d_layer_msg_vw.resize(nl);
   h->layer_msg_vw.resize(nl);
@@ -1236,7 +1271,7 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->TA || !h->mrt || !h->drt || !h->msg ||
       !h->raw || !h->gram || !h->dmat ||
-      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho) {
+      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho || !h->rx_cs) {
     set_error("device allocation failed (footprint " + std::to_string(footprint_of(g, chi)) +
               " bytes)");
     return fail(TN_ENOMEM);
@@ -1346,17 +1381,22 @@ const char* tn_profile_class_name(int32_t cls) {
   return kProfNames[cls];
 }
 
-static tn_status evolve(tn_handle* h, double theta, int steps, bool clifford_dagger) {
+static tn_status evolve(tn_handle* h, double theta, int steps, bool clifford_dagger,
+                        const double* theta_v = nullptr) {
   if (!h) { set_error("null handle"); return TN_EINVAL; }
   if (steps < 0) { set_error("steps must be >= 0"); return TN_EINVAL; }
   h->stats = tn_stats{};
   tn_status worst = TN_OK;
   double u[8];
   rx_matrix(clifford_dagger ? -M_PI / 2 : theta, u);
+  if (theta_v) {
+    tn_status st = upload_rx_field(h, theta_v);
+    if (st) return st;
+  }
   for (int s = 0; s < steps; ++s) {
     tn_status st;
     if (!clifford_dagger) {
-      st = phys_gate(h, u);
+      st = theta_v ? phys_gate_field(h) : phys_gate(h, u);
       if (st) return st;
     }
     for (int li = 0; li < (int)h->g.layers.size(); ++li) {
@@ -1378,6 +1418,14 @@ static tn_status evolve(tn_handle* h, double theta, int steps, bool clifford_dag
 
 tn_status tn_apply_floquet(tn_handle* h, double theta_h, int32_t steps) {
   return evolve(h, theta_h, steps, false);
+}
+
+tn_status tn_apply_floquet_field(tn_handle* h, const double* theta_v, int32_t steps) {
+  if (!h) { set_error("null handle"); return TN_EINVAL; }
+  if (!theta_v) { set_error("theta_v is null"); return TN_EINVAL; }
+  for (int v = 0; v < h->g.n; ++v)
+    if (!std::isfinite(theta_v[v])) { set_error("theta_v holds a non-finite angle"); return TN_EINVAL; }
+  return evolve(h, 0.0, steps, false, theta_v);
 }
 
 tn_status tn_apply_clifford_dagger(tn_handle* h, int32_t steps) {

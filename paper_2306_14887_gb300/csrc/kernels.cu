@@ -2,6 +2,8 @@
 // that carries every contraction of the message and gate updates in the
 // TN_FP32 mode, the physical-leg gate, message normalisation with the FP64
 // residual, the single-site reduced density matrix and a batched block copy.
+#include <mutex>
+
 #include "common.cuh"
 #include "tnbp.h"
 
@@ -153,6 +155,38 @@ __global__ void phys_gate_kernel(float* T, const int64_t* site_off, int64_t len,
   }
 }
 }  // namespace
+
+namespace {
+// RX(theta_v) = [[c, -i s], [-i s, c]] with (c, s) = (cos theta_v/2, sin theta_v/2)
+// per site: the kicks of many instances batched in one graph.
+__global__ void phys_gate_field_kernel(float* T, const int64_t* site_off, const float2* cs,
+                                       int64_t len, int64_t plane) {
+  const int64_t base = site_off[blockIdx.y];
+  const float c = cs[blockIdx.y].x, sn = cs[blockIdx.y].y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float* t0r = T + base + i;
+    float* t1r = T + base + len + i;
+    const float ar = t0r[0], ai = t0r[plane];
+    const float br = t1r[0], bi = t1r[plane];
+    // c a - i s b, -i s a + c b
+    t0r[0] = c * ar + sn * bi;
+    t0r[plane] = c * ai - sn * br;
+    t1r[0] = sn * ai + c * br;
+    t1r[plane] = -sn * ar + c * bi;
+  }
+}
+}  // namespace
+
+cudaError_t launch_phys_gate_field(float* T, const int64_t* site_off, const float2* cs,
+                                   int n_sites, int64_t len, int64_t plane, cudaStream_t s) {
+  if (n_sites <= 0) return cudaSuccess;
+  int64_t bx = (len + 255) / 256;
+  if (bx > 1024) bx = 1024;
+  dim3 grid((unsigned)bx, n_sites);
+  phys_gate_field_kernel<<<grid, 256, 0, s>>>(T, site_off, cs, len, plane);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_phys_gate(float* T, const int64_t* site_off, int n_sites, int64_t len,
                              int64_t plane, float u00r, float u00i, float u01r, float u01i,
@@ -358,15 +392,16 @@ cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site
   return cudaGetLastError();
 }
 
-static int g_norm_attr_bytes = 48 * 1024;
-
-cudaError_t normalise_prepare(int chi) {
-  const size_t sm = sizeof(float) * 2 * (size_t)chi * (chi + 1);
-  if (sm > 200 * 1024 || (int)sm <= g_norm_attr_bytes) return cudaSuccess;
-  cudaError_t e =
-      cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e == cudaSuccess) g_norm_attr_bytes = (int)sm;
-  return e;
+// The shared-memory limit of the normalise kernel, raised once to the largest
+// tile the kernel takes (chi with 2 chi (chi + 1) floats <= 200 KB); thread-safe.
+cudaError_t normalise_prepare(int) {
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] {
+    result = cudaFuncSetAttribute(normalise_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024);
+  });
+  return result;
 }
 
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,

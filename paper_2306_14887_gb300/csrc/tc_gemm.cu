@@ -28,6 +28,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "tc_common.cuh"
 #include "tnbp.h"
@@ -613,16 +615,17 @@ bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {
 
 // Kernel attributes, set once before any launch (and before any stream capture).
 cudaError_t tc_prepare() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_smem_bytes(1));
-  if (e != cudaSuccess) return e;
-  // two CTAs per SM: ask for the largest shared-memory carveout
-  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e != cudaSuccess) return e;
-  done = true;
-  return cudaSuccess;
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] {
+    result = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem_bytes(1));
+    // two CTAs per SM: ask for the largest shared-memory carveout
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    100);
+  });
+  return result;
 }
 
 cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t st,

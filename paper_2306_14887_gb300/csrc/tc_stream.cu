@@ -30,6 +30,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "tc_common.cuh"
 #include "tnbp.h"
@@ -425,10 +427,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
+  static std::once_flag once;
   static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
@@ -437,7 +438,7 @@ EncodeTiledFn encode_fn() {
       fn = reinterpret_cast<EncodeTiledFn>(p);
     else
       cudaGetLastError();
-  }
+  });
   return fn;
 }
 
@@ -556,18 +557,24 @@ bool tc_stream_encode(const GemmDesc& d, const float* const* A, const float* con
 size_t tc_stream_map_bytes(int n_outer) { return (size_t)2 * n_outer * sizeof(CUtensorMap); }
 
 cudaError_t tc_stream_prepare() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(tc_stream_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (e != cudaSuccess) return e;
-  int dev = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  done = true;
-  return cudaSuccess;
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] {
+    result = cudaFuncSetAttribute(tc_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kSmemBytes);
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(tc_close_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kCSmemBytes);
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(tc_close_kernel,
+                                    cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int dev = 0, sms = 0;
+    if (result == cudaSuccess) result = cudaGetDevice(&dev);
+    if (result == cudaSuccess)
+      result = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (result == cudaSuccess) g_num_sms = sms;
+  });
+  return result;
 }
 
 cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err, cudaStream_t st) {
@@ -638,14 +645,9 @@ bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* cons
 
 cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* part, int* err,
                             cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_close_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCSmemBytes);
+  {
+    cudaError_t e = tc_stream_prepare();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(tc_close_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    attr = true;
   }
   CloseArgs a;
   a.maps = reinterpret_cast<const CUtensorMap*>(p.maps);

@@ -121,3 +121,28 @@ def test_create_without_gpu_reports_cuda_error():
     st = L.tn_create(C.byref(g), C.byref(cfg), None, None, C.byref(h))
     assert st == -6
     assert "CUDA" in L.tn_last_error().decode() or "device" in L.tn_last_error().decode()
+
+
+def test_batch_union_offsets_and_colouring():
+    from oracle import graph as OG
+    gs = [OG.ring(12), OG.falcon27_patch(), OG.ring(12)]
+    n, edges, cols, offs = tn.batch_union([(g.n, g.edges, g.colours) for g in gs])
+    assert n == 12 + 27 + 12 and offs == [0, 12, 39]
+    assert len(edges) == sum(len(g.edges) for g in gs) and len(cols) == len(edges)
+    # components stay disjoint and each keeps a proper colouring
+    for g, off in zip(gs, offs):
+        sub = [tuple(e) for e in edges if off <= e[0] < off + g.n]
+        assert len(sub) == len(g.edges)
+        assert all(off <= a < off + g.n and off <= b < off + g.n for a, b in sub)
+    seen = {}
+    for (a, b), c in zip(edges, cols):
+        for v in (a, b):
+            assert (v, c) not in seen
+            seen[(v, c)] = True
+
+
+def test_server_rejects_bad_config_before_touching_a_device():
+    cfg = tn.tn_server_config()
+    cfg.max_slots = 0
+    h = tn.C.c_void_p()
+    assert tn.lib().tn_server_create(tn.C.byref(cfg), tn.C.byref(h)) == -1
