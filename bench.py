@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--presteps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--serve-jobs", type=int, default=16,
+                   help="jobs of the serving leg (0: skip)")
     return p.parse_args()
 
 
@@ -97,6 +99,54 @@ def max_over_ranks(ms, device):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.barrier()
     return float(t.item())
+
+
+def workload_config(args, world):
+    """The workload both arms report (the reference arm times the oracle on it)."""
+    chi = args.chi
+    presteps = args.presteps if args.presteps is not None else int(np.log2(max(chi, 1))) + 1
+    theta = theta_for(0, args)
+    return {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, solve={args.solve}, "
+                        f"theta_h={theta:.4f}, saturated after {presteps} steps",
+            "qubits": 127, "edges": 144, "chi": chi,
+            "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
+                (36 * 4 * chi ** 3 + 89 * 4 * chi ** 2 + 2 * 4 * chi) * 4 / 1e6),
+            "parallelism": f"theta-sharded x{world}" if world > 1 else "single GPU"}
+
+
+def serve_leg(tn, args):
+    """p50 / p99 latency of a bounded sample of the serving workload: the first
+    jobs of the seeded Poisson stream (200 jobs/s) whose graph has at most 127
+    qubits and chi at most 64, submitted at their arrival times to a server with
+    4 slots; latency is arrival to result."""
+    from workloads import serving_jobs
+    n, edges, cols = eagle()
+    keep = np.all(edges < 27, axis=1)  # the 27-qubit patch: qubits 0..26 of the layout
+    graphs = {27: (27, edges[keep], cols[keep]), 127: (n, edges, cols)}
+    stream = [j for j in serving_jobs(n=2000) if j[1] in graphs and j[2] <= 64][:args.serve_jobs]
+    lat, steps_done = [], 0
+    with tn.Server(slots=4) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (arr, size, chi, theta, steps) in stream:
+            while time.perf_counter() - t0 < arr - stream[0][0]:
+                time.sleep(0.0005)
+            gn, ge, gc = graphs[size]
+            tickets.append(srv.submit(gn, ge, gc, chi, theta, steps, prec=args.prec))
+        for t in tickets:
+            z, info = srv.wait(t)
+            lat.append(info["latency_s"])
+            steps_done += info["steps_done"]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.array(lat)
+    return {"jobs": len(lat), "slots": 4, "arrival_rate_per_s": 200.0,
+            "p50_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_s": round(float(np.percentile(lat, 99)), 4),
+            "steps_per_s": round(steps_done / wall, 3), "peak_resident": st["peak_resident"],
+            "sample": "first %d jobs of the seeded stream with <= 127 qubits and chi <= 64 "
+                      "(27- and 127-qubit graphs, chi 16/32/64, 5-20 steps), prec %s"
+                      % (len(lat), args.prec)}
 
 
 def eagle():
@@ -347,6 +397,9 @@ def run_ours(args, rank, world, local):
     shared_solve = args.solve == "shared" or (args.solve == "auto" and args.prec != "fp32")
     rl = roofline(prof, args.prec, chi, bp_iters, nbd, shared_solve)
     rl["share_of_timed"] = round(prof[rl["kernel"]]["ms"] / ms, 4)
+    serving = None
+    if args.serve_jobs > 0 and rank == 0:
+        serving = serve_leg(tn, args)
     fp32_line = None
     if args.fp32_steps > 0 and args.prec != "fp32":
         s3 = tn.TNState(n, edges, cols, chi=chi, prec="fp32", stream=stream)
@@ -373,12 +426,7 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16": "bf16"}.get(args.prec, args.prec),
         "data": "synthetic (initial state |0..0>, theta_h from the uniform [0, pi/2] grid)",
-        "config": {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, solve={args.solve}, "
-                               f"theta_h={theta:.4f}, saturated after {presteps} steps",
-                   "qubits": int(n), "edges": int(len(edges)), "chi": chi,
-                   "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
-                       (36 * 4 * chi ** 3 + 89 * 4 * chi ** 2 + 2 * 4 * chi) * 4 / 1e6),
-                   "parallelism": f"theta-sharded x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(args, world),
         "gpu_launches": int(launches),
         "tma_stream_launches": int(tma_launches),
         "bp_sweeps_per_step": round(bp_iters / args.steps, 2),
@@ -389,6 +437,7 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "z_mean": float(np.mean(z)),
         "fp32_path": fp32_line,
+        "serving": serving,
     }
     if fp32_line:
         fp32_line["mixed_over_fp32"] = round(value / world / fp32_line["value"], 3)
@@ -428,7 +477,7 @@ def run_reference(args, rank, world):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(per * 1e3, 2), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"eagle127 heavy-hex, chi={chi}, FP64 CPU oracle"},
+           "config": workload_config(args, world),
            "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": blas_threads(),
                             "kind": "oracle",
                             "sample": "each step: one BP sweep + 2 simple-update gates on a random "
