@@ -221,38 +221,55 @@ __device__ double block_sum(double v, double* sh) {
   return sh[0];
 }
 
+// s + c += a^2 without rounding loss: the square split exactly by FMA
+// (a a = p + e), the sum kept as an unevaluated pair (s, c) by Knuth's
+// two-sum.  About 48 significant bits from FP32 operations, so the per-element
+// work avoids the FP64 pipe (1/64 of the FP32 rate on this part).
+__device__ __forceinline__ void pair_add_sq(float& s, float& c, float a) {
+  const float p = __fmul_rn(a, a);  // not contracted into the sum below
+  const float e = fmaf(a, a, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  c += (__fsub_rn(s, __fsub_rn(t, bp)) + __fsub_rn(p, bp)) + e;
+  s = t;
+}
+
 // Large chi: the transposed entry is read from global memory.
 __global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
                                       unsigned long long* res_bits, int* flags) {
   __shared__ double sh[32];
   const int64_t n2 = (int64_t)chi * chi;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float* r = raw + blockIdx.x * 2 * n2;
   float* m = msg + blockIdx.x * 2 * n2;
-  double ss = 0.0;
-  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
-    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    const double hr = 0.5 * ((double)r[idx] + (double)r[(int64_t)j * chi + i]);
-    const double hi = 0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]);
-    ss += hr * hr + hi * hi;
-  }
-  ss = block_sum(ss, sh);
+  float s0 = 0.f, c0 = 0.f;
+  for (int i = warp; i < chi; i += nw)
+    for (int j = lane; j < chi; j += 32) {
+      const int64_t a = (int64_t)i * chi + j, t = (int64_t)j * chi + i;
+      pair_add_sq(s0, c0, 0.5f * (r[a] + r[t]));
+      pair_add_sq(s0, c0, 0.5f * (r[n2 + a] - r[n2 + t]));
+    }
+  const double ss = block_sum((double)s0 + (double)c0, sh);
   const double nrm = sqrt(ss);
   if (!(nrm > 0.0) || !isfinite(nrm)) {
     if (threadIdx.x == 0) atomicOr(flags, 1);
     return;
   }
-  const double inv = 1.0 / nrm;
-  double dd = 0.0;
-  for (int64_t idx = threadIdx.x; idx < n2; idx += blockDim.x) {
-    const int i = (int)(idx / chi), j = (int)(idx - (int64_t)i * chi);
-    const double hr = 0.5 * ((double)r[idx] + (double)r[(int64_t)j * chi + i]) * inv;
-    const double hi = 0.5 * ((double)r[n2 + idx] - (double)r[n2 + (int64_t)j * chi + i]) * inv;
-    const double er = hr - (double)m[idx], ei = hi - (double)m[n2 + idx];
-    dd += er * er + ei * ei;
-    m[idx] = (float)hr;
-    m[n2 + idx] = (float)hi;
-  }
-  dd = block_sum(dd, sh);
+  const float inv = (float)(1.0 / nrm);
+  // all reads of the raw message precede the writes of the normalised one
+  // (different buffers), so the loop may overwrite m as it goes
+  float d0 = 0.f, dc = 0.f;
+  for (int i = warp; i < chi; i += nw)
+    for (int j = lane; j < chi; j += 32) {
+      const int64_t a = (int64_t)i * chi + j, t = (int64_t)j * chi + i;
+      const float hr = 0.5f * (r[a] + r[t]) * inv;
+      const float hi = 0.5f * (r[n2 + a] - r[n2 + t]) * inv;
+      pair_add_sq(d0, dc, hr - m[a]);
+      pair_add_sq(d0, dc, hi - m[n2 + a]);
+      m[a] = hr;
+      m[n2 + a] = hi;
+    }
+  const double dd = block_sum((double)d0 + (double)dc, sh);
   if (threadIdx.x == 0) {
     const double res = sqrt(dd);
     atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
@@ -281,21 +298,22 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
   __syncthreads();
   // H = (R + R^H) / 2: element (i, j) with the transposed read from the padded
   // tile (consecutive lanes, consecutive j: distinct banks); sums in FP64
-  double ss = 0.0;
+  float s0 = 0.f, c0 = 0.f;
   for (int i = warp; i < chi; i += nw)
     for (int j = lane; j < chi; j += 32) {
-      const double hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]);
-      const double hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]);
-      ss = fma(hr, hr, fma(hi, hi, ss));
+      const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]);
+      const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]);
+      pair_add_sq(s0, c0, hr);
+      pair_add_sq(s0, c0, hi);
     }
-  ss = block_sum(ss, sh);
+  double ss = block_sum((double)s0 + (double)c0, sh);
   const double nrm = sqrt(ss);
   if (!(nrm > 0.0) || !isfinite(nrm)) {
     if (threadIdx.x == 0) atomicOr(flags, 1);
     return;
   }
   const float inv = (float)(1.0 / nrm);
-  double dd = 0.0;
+  float d0 = 0.f, dc = 0.f;
   float* q = mrt ? mrt + (int64_t)blockIdx.x * 4 * n2 : nullptr;
   const int w = 2 * chi;
   for (int i = warp; i < chi; i += nw)
@@ -303,9 +321,9 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
       const int idx = i * chi + j;
       const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]) * inv;
       const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]) * inv;
-      // the difference of two nearby FP32 values is exact; squared and summed in FP64
-      const double er = hr - m[idx], ei = hi - m[n2 + idx];
-      dd = fma(er, er, fma(ei, ei, dd));
+      // the difference of two nearby FP32 values is exact
+      pair_add_sq(d0, dc, hr - m[idx]);
+      pair_add_sq(d0, dc, hi - m[n2 + idx]);
       m[idx] = hr;
       m[n2 + idx] = hi;
       if (q) {
@@ -319,7 +337,7 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
         q[i * w + chi + j] = hi;
       }
     }
-  dd = block_sum(dd, sh);
+  const double dd = block_sum((double)d0 + (double)dc, sh);
   if (threadIdx.x == 0) {
     const double res = sqrt(dd);
     atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));

@@ -389,16 +389,24 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   const int half = n / 2;
   int sweeps = 0;
   if (n % 32 == 0) {
-    // Rows of 2 x 16-byte vectors: each pair is owned by 16 lanes (two pairs per
+    // Rows of 2 x 16-byte vectors, each pair owned by 16 lanes (two pairs per
     // warp, so the rotation arithmetic serves two pairs), lane l holding the
-    // vectors l, l + 16, ... of both rows (consecutive lanes, consecutive
-    // addresses).  Squared row norms live in shared memory: recomputed exactly
-    // at the start of each sweep and updated by each rotation, which moves
-    // t |gamma| of weight from row p to row q (alpha' = alpha - t|g|,
-    // beta' = beta + t|g|).
+    // vectors l, l + 16, ... of a row (consecutive lanes, consecutive
+    // addresses).  Pair order: recursive halving.  At level B (B = n/2, n/4,
+    // .., 1) the rows form groups of 2B; slot s = g B + i keeps row g 2B + i
+    // ("stationary") in registers for the B rounds of the level and meets
+    // row g 2B + B + (i + r) mod B in round r, so every pair of rows meets
+    // exactly once per sweep in n - 1 rounds, as in the round-robin order,
+    // while only the partner row passes through shared memory each round
+    // (shared-memory bandwidth bounds this loop).  Squared row norms:
+    // recomputed exactly at the start of each sweep, updated by each rotation,
+    // which moves t |gamma| of weight from row p to row q
+    // (alpha' = alpha - t|g|, beta' = beta + t|g|).
     float4* X4 = reinterpret_cast<float4*>(X);
     const int row4 = n / 2, nq = n / 32;
     const int sub = lane >> 4, gl = lane & 15;
+    const int slot = warp * 2 + sub;
+    const bool active = 2 * warp < half;  // warp-uniform: half is even
     for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
       ++sweeps;
       for (int j = warp; j < n; j += kWarps) {
@@ -412,83 +420,93 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
       }
       __syncthreads();
       int any = 0;
-      for (int r = 0; r < n - 1; ++r) {
-        const int k = warp * 2 + sub;
-        int rot = 0;
-        if (2 * warp < half) {  // warp-uniform: half is even
-          int p, q;
-          if (k == 0) { p = r; q = n - 1; }
-          else { p = (r + k) % (n - 1); q = (r - k + (n - 1)) % (n - 1); }
-          // (the rows are read twice, for gamma and for the rotation, to stay
-          // within the 64 registers a thread of a 1024-thread block has)
-          float gr = 0.f, gi = 0.f;
+      for (int B = half; B >= 1; B >>= 1) {
+        const int g = slot / B, i = slot - g * B;
+        const int prow = g * 2 * B + i;
+        float4 xs[4];
+        float al = 0.f;
+        if (active) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (u < nq) {
-              const float4 xp = X4[p * row4 + gl + 16 * u];
-              const float4 xq = X4[q * row4 + gl + 16 * u];
-              // gamma = sum conj(xp) xq over the two complex values of the vector
-              gr += xp.x * xq.x + xp.y * xq.y + xp.z * xq.z + xp.w * xq.w;
-              gi += xp.x * xq.y - xp.y * xq.x + xp.z * xq.w - xp.w * xq.z;
-            }
-          }
-#pragma unroll
-          for (int o = 8; o > 0; o >>= 1) {
-            gr += __shfl_xor_sync(0xffffffffu, gr, o);
-            gi += __shfl_xor_sync(0xffffffffu, gi, o);
-          }
-          const float al = s.nrm[p], be = s.nrm[q];
-          const float g2 = gr * gr + gi * gi;
-          // |gamma| > orth_tol sqrt(al be) and |gamma| > abs_floor, compared squared
-          if (g2 > orth_tol2 * al * be && g2 > abs_floor2 && g2 > 0.f) {
-            // 1/|gamma| and cos = 1/sqrt(1 + t^2) from the hardware reciprocal
-            // square root refined by one step of Newton's iteration
-            // y <- y (3 - x y^2) / 2: the phase e^{-i phi} and the pair (cos, sin)
-            // are then unit to about one ulp, so the rotations stay unitary and
-            // the row norms do not drift.  t itself may be approximate: any t
-            // gives a unitary rotation, and an inexact angle only leaves a
-            // residual overlap that later rounds remove.
-            float ig = rsqrtf(g2);
-            ig = ig * (1.5f - 0.5f * g2 * ig * ig);
-            const float gm = g2 * ig;
-            const float2 ph = make_float2(gr * ig, -gi * ig);  // e^{-i phi}
-            const float tau = (be - al) * 0.5f * ig;
-            const float at = fabsf(tau);
-            float t;
-            if (at < 1e15f) {
-              const float q1 = 1.f + at * at;
-              t = __fdividef(1.f, at + q1 * rsqrtf(q1));  // 1 / (|tau| + sqrt(1 + tau^2))
-            } else {
-              t = 0.5f / at;
-            }
-            if (tau < 0.f) t = -t;
-            const float q2 = 1.f + t * t;
-            float cs = rsqrtf(q2);
-            cs = cs * (1.5f - 0.5f * q2 * cs * cs);
-            const float sn = t * cs;
+          for (int u = 0; u < 4; ++u)
+            if (u < nq) xs[u] = X4[prow * row4 + gl + 16 * u];
+          al = s.nrm[prow];
+        }
+        for (int r = 0; r < B; ++r) {
+          int rot = 0;
+          if (active) {
+            const int q = g * 2 * B + B + (i + r) % B;
+            float4 xq[4];
+            float gr = 0.f, gi = 0.f;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               if (u < nq) {
-                const float4 xp = X4[p * row4 + gl + 16 * u];
-                const float4 xq = X4[q * row4 + gl + 16 * u];
-                const float2 q0 = cmulf(ph, make_float2(xq.x, xq.y));
-                const float2 q1 = cmulf(ph, make_float2(xq.z, xq.w));
-                X4[p * row4 + gl + 16 * u] =
-                    make_float4(cs * xp.x - sn * q0.x, cs * xp.y - sn * q0.y,
-                                cs * xp.z - sn * q1.x, cs * xp.w - sn * q1.y);
-                X4[q * row4 + gl + 16 * u] =
-                    make_float4(sn * xp.x + cs * q0.x, sn * xp.y + cs * q0.y,
-                                sn * xp.z + cs * q1.x, sn * xp.w + cs * q1.y);
+                xq[u] = X4[q * row4 + gl + 16 * u];
+                // gamma = sum conj(x_p) x_q over the two complex values of the vector
+                gr += xs[u].x * xq[u].x + xs[u].y * xq[u].y + xs[u].z * xq[u].z + xs[u].w * xq[u].w;
+                gi += xs[u].x * xq[u].y - xs[u].y * xq[u].x + xs[u].z * xq[u].w - xs[u].w * xq[u].z;
               }
             }
-            if (gl == 0) {
-              s.nrm[p] = fmaxf(al - t * gm, 0.f);
-              s.nrm[q] = be + t * gm;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+              gr += __shfl_xor_sync(0xffffffffu, gr, o);
+              gi += __shfl_xor_sync(0xffffffffu, gi, o);
             }
-            rot = 1;
+            const float be = s.nrm[q];
+            const float g2 = gr * gr + gi * gi;
+            // |gamma| > orth_tol sqrt(al be) and |gamma| > abs_floor, compared squared
+            if (g2 > orth_tol2 * al * be && g2 > abs_floor2 && g2 > 0.f) {
+              // 1/|gamma| and cos = 1/sqrt(1 + t^2) from the hardware reciprocal
+              // square root refined by one step of Newton's iteration
+              // y <- y (3 - x y^2) / 2: the phase e^{-i phi} and the pair (cos, sin)
+              // are then unit to about one ulp, so the rotations stay unitary and
+              // the row norms do not drift.  t itself may be approximate: any t
+              // gives a unitary rotation, and an inexact angle only leaves a
+              // residual overlap that later rounds remove.
+              float ig = rsqrtf(g2);
+              ig = ig * (1.5f - 0.5f * g2 * ig * ig);
+              const float gm = g2 * ig;
+              const float2 ph = make_float2(gr * ig, -gi * ig);  // e^{-i phi}
+              const float tau = (be - al) * 0.5f * ig;
+              const float at = fabsf(tau);
+              float t;
+              if (at < 1e15f) {
+                const float q1 = 1.f + at * at;
+                t = __fdividef(1.f, at + q1 * rsqrtf(q1));  // 1 / (|tau| + sqrt(1 + tau^2))
+              } else {
+                t = 0.5f / at;
+              }
+              if (tau < 0.f) t = -t;
+              const float q2 = 1.f + t * t;
+              float cs = rsqrtf(q2);
+              cs = cs * (1.5f - 0.5f * q2 * cs * cs);
+              const float sn = t * cs;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if (u < nq) {
+                  const float2 q0 = cmulf(ph, make_float2(xq[u].x, xq[u].y));
+                  const float2 q1 = cmulf(ph, make_float2(xq[u].z, xq[u].w));
+                  const float4 xp = xs[u];
+                  xs[u] = make_float4(cs * xp.x - sn * q0.x, cs * xp.y - sn * q0.y,
+                                      cs * xp.z - sn * q1.x, cs * xp.w - sn * q1.y);
+                  X4[q * row4 + gl + 16 * u] =
+                      make_float4(sn * xp.x + cs * q0.x, sn * xp.y + cs * q0.y,
+                                  sn * xp.z + cs * q1.x, sn * xp.w + cs * q1.y);
+                }
+              }
+              al = fmaxf(al - t * gm, 0.f);
+              if (gl == 0) s.nrm[q] = be + t * gm;
+              rot = 1;
+            }
           }
+          any |= __syncthreads_or(rot);
         }
-        any |= __syncthreads_or(rot);
+        if (active) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (u < nq) X4[prow * row4 + gl + 16 * u] = xs[u];
+          if (gl == 0) s.nrm[prow] = al;
+        }
+        __syncthreads();
       }
       if (!any) break;
     }
