@@ -235,8 +235,13 @@ typedef struct {
  * gauge": the environment of a region is the product of its incoming BP
  * messages).  Weight-1 strings use rho_v[p, p'] = sum T_v[p, ..] conj(T_v[p', ..])
  * prod_x M_{x->v} and <P> = Tr(rho P) / Tr(rho).
- * method 0: strings of weight > 1 are contracted exactly over a tree spanning
- *           their support, every other edge closed by the converged messages.
+ * method 0: strings of weight > 1 are contracted exactly over a tree T_S
+ *           spanning their support, every edge leaving T_S closed by its
+ *           converged message, and divided by the same contraction without the
+ *           operators.  T_S: breadth-first search from the smallest support site
+ *           (neighbours in increasing edge id), the union of the search-tree
+ *           paths from the other support sites.  Errors: TN_ENUMERIC when the
+ *           region's norm contraction vanishes.
  * method 1: "extended time evolution": the library finds (i, n') with
  *           string = +-U^n'(pi/2) Z_i U^n'(pi/2)^dagger by Pauli propagation, evolves
  *           a copy of the state by U(pi/2)^dagger n' times and measures Z_i;

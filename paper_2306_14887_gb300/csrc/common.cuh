@@ -115,6 +115,8 @@ cudaError_t normalise_prepare(int chi);
 // RX-type 2x2 on the physical leg: T[p] <- sum_q U[p][q] T[q] for every site in
 // the list.  site_off: float offset of each site's real plane; len: chi^d
 // complex entries per physical value; plane: 2*chi^d.
+cudaError_t launch_scale_unit(float* m, int chi, double* logacc, int* zero, cudaStream_t s);
+cudaError_t launch_dot_msgs(const float* R, const float* M, int chi, double* out, cudaStream_t s);
 cudaError_t launch_phys_gate_field(float* T, const int64_t* site_off, const float2* cs,
                                    int n_sites, int64_t len, int64_t plane, cudaStream_t s);
 cudaError_t launch_phys_gate(float* T, const int64_t* site_off, int n_sites, int64_t len,

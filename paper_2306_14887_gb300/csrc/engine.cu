@@ -158,6 +158,17 @@ void* dev_alloc(tn_handle* h, size_t bytes) {
   return p;
 }
 
+void dev_free(tn_handle* h, void* p) {
+  for (size_t i = 0; i < h->allocations.size(); ++i) {
+    if (h->allocations[i].first != p) continue;
+    if (h->own_alloc) cudaFree(p);
+    else h->alloc.free(p, h->allocations[i].second, h->alloc.ctx, (void*)h->stream);
+    h->bytes -= h->allocations[i].second;
+    h->allocations.erase(h->allocations.begin() + i);
+    return;
+  }
+}
+
 void dev_free_all(tn_handle* h) {
   for (auto& a : h->allocations) {
     if (h->own_alloc) cudaFree(a.first);
@@ -508,31 +519,46 @@ const float* in_mrt(const tn_handle* h, int v, int e) {
 //   B1  Y1[(p,b,c')][a]   = T  x_c Mc        B2  Y2[b][p][a'][c'] = Y1 x_a Ma
 //   C1  Y1[(p,c,a')][b]   = TA x_a Ma        C2  Y2[c][p][b'][a'] = Y1 x_b Mb
 // each followed by the close on the open leg against T (chains A, B) or TA (C).
-void deg3_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites, bool open_p,
-                const std::vector<float*>& outs) {
+// Operands of one site's chain: ket tensor and its first-leg-last copy, the
+// bra (the same tensor, or the tensor with an operator applied on p) and its
+// copy, the site's intermediate slots, the realified transposed incoming
+// message per leg position, and the output.
+struct ChainSite {
+  const float *T, *TA, *bra, *braA, *Y1, *Y2;
+  const float* m[3];
+  float* out;
+};
+
+ChainSite handle_site(const tn_handle* h, int v, float* out) {
+  const auto& lg = h->g.legs[v];
+  ChainSite c;
+  c.T = c.bra = site_ptr(h, h->T, v);
+  c.TA = c.braA = site_ptr(h, h->TA, v);
+  c.Y1 = site_ptr(h, h->Y1, v);
+  c.Y2 = site_ptr(h, h->Y2, v);
+  for (int j = 0; j < 3; ++j) c.m[j] = j < (int)lg.size() ? in_mrt(h, v, lg[j]) : nullptr;
+  c.out = out;
+  return c;
+}
+
+void deg3_chain_sites(tn_handle* h, Plan& P, int which, const std::vector<ChainSite>& cs,
+                      bool open_p) {
   const int x = h->chi, prec = h->cfg.prec;
   const int64_t x2 = (int64_t)x * x, x3 = x2 * x, plane = 2 * x3;
-  const HostGraph& g = h->g;
   std::vector<Ent> e1, e2, ec;
-  for (size_t i = 0; i < sites.size(); ++i) {
-    const int v = sites[i];
-    const auto& lg = g.legs[v];
-    const float* T = site_ptr(h, h->T, v);
-    const float* TA = site_ptr(h, h->TA, v);
-    const float* Y1 = site_ptr(h, h->Y1, v);
-    const float* Y2 = site_ptr(h, h->Y2, v);
+  for (const ChainSite& c : cs) {
     if (which == 0) {
-      e1.push_back({T, in_mrt(h, v, lg[2]), Y1});
-      e2.push_back({Y1, in_mrt(h, v, lg[1]), Y2});
-      ec.push_back({Y2, T, outs[i]});
+      e1.push_back({c.T, c.m[2], c.Y1});
+      e2.push_back({c.Y1, c.m[1], c.Y2});
+      ec.push_back({c.Y2, c.bra, c.out});
     } else if (which == 1) {
-      e1.push_back({T, in_mrt(h, v, lg[2]), Y1});
-      e2.push_back({Y1, in_mrt(h, v, lg[0]), Y2});
-      ec.push_back({Y2, T, outs[i]});
+      e1.push_back({c.T, c.m[2], c.Y1});
+      e2.push_back({c.Y1, c.m[0], c.Y2});
+      ec.push_back({c.Y2, c.bra, c.out});
     } else {
-      e1.push_back({TA, in_mrt(h, v, lg[0]), Y1});
-      e2.push_back({Y1, in_mrt(h, v, lg[1]), Y2});
-      ec.push_back({Y2, TA, outs[i]});
+      e1.push_back({c.TA, c.m[0], c.Y1});
+      e2.push_back({c.Y1, c.m[1], c.Y2});
+      ec.push_back({c.Y2, c.braA, c.out});
     }
   }
   const int M = (int)(2 * x2);
@@ -566,22 +592,27 @@ void deg3_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites,
   add_spec(P, sc, prec, ec);
 }
 
+void deg3_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites, bool open_p,
+                const std::vector<float*>& outs) {
+  std::vector<ChainSite> cs;
+  for (size_t i = 0; i < sites.size(); ++i) cs.push_back(handle_site(h, sites[i], outs[i]));
+  deg3_chain_sites(h, P, which, cs, open_p);
+}
+
 // Degree-2 chains (T[p][a][b], TA[p][b][a]):
 //   which 0: Y1[a][p][b'] = T x_b Mb, close on a against T
 //   which 1: Y1[b][p][a'] = TA x_a Ma, close on b against TA
-void deg2_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites, bool open_p,
-                const std::vector<float*>& outs) {
+void deg2_chain_sites(tn_handle* h, Plan& P, int which, const std::vector<ChainSite>& cs,
+                      bool open_p) {
   const int x = h->chi, prec = h->cfg.prec;
   const int64_t x2 = (int64_t)x * x, plane = 2 * x2;
-  const HostGraph& g = h->g;
   std::vector<Ent> e1, ec;
-  for (size_t i = 0; i < sites.size(); ++i) {
-    const int v = sites[i];
-    const auto& lg = g.legs[v];
-    const float* src = site_ptr(h, which == 0 ? h->T : h->TA, v);
-    const float* Y1 = site_ptr(h, which == 0 ? h->Y1 : h->Y2, v);
-    e1.push_back({src, in_mrt(h, v, lg[which == 0 ? 1 : 0]), Y1});
-    ec.push_back({Y1, src, outs[i]});
+  for (const ChainSite& c : cs) {
+    const float* src = which == 0 ? c.T : c.TA;
+    const float* bra = which == 0 ? c.bra : c.braA;
+    const float* Y1 = which == 0 ? c.Y1 : c.Y2;
+    e1.push_back({src, c.m[which == 0 ? 1 : 0], Y1});
+    ec.push_back({Y1, bra, c.out});
   }
   // rows (p, l) of the source -> Y1 at l 2x + p x + n
   Spec s1 = mode_spec(x, plane, (int)(2 * x), x, 1, x2, x, 0, x, 2 * x, 0, 1);
@@ -589,6 +620,14 @@ void deg2_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites,
   if (open_p) { sc.K1 = 1; sc.n_inner = 2; sc.a_in = x; sc.b_in = x2; sc.c_in = 2 * x2; }
   add_spec(P, s1, prec, e1);
   add_spec(P, sc, prec, ec);
+}
+
+
+void deg2_chain(tn_handle* h, Plan& P, int which, const std::vector<int>& sites, bool open_p,
+                const std::vector<float*>& outs) {
+  std::vector<ChainSite> cs;
+  for (size_t i = 0; i < sites.size(); ++i) cs.push_back(handle_site(h, sites[i], outs[i]));
+  deg2_chain_sites(h, P, which, cs, open_p);
 }
 
 void build_sweep_plan(tn_handle* h) {
@@ -1476,6 +1515,211 @@ static tn_status backup_state(tn_handle* h, bool restore) {
   return TN_OK;
 }
 
+
+// ------------------------------------------------------------ region strings
+// A Pauli string of weight k > 1 by the BP-region reading of the expectation
+// rule (Methods, "Measuring expectation values within the Vidal gauge"; the
+// environment of a region is the product of the converged messages entering
+// it): exact contraction of the norm network over a tree T_S spanning the
+// string's support, every edge leaving the tree closed by its converged
+// message, divided by the same contraction without the operators.
+//
+// Tree rule: breadth-first search from the smallest support site, neighbours
+// in increasing edge id; T_S is the union of the search-tree paths from the
+// other support sites back to it.  Contraction: sites in post-order from the
+// root (the smallest vertex of T_S); each non-root site sends its parent the
+// BP message update of its norm tensor with the operator inserted on the bra's
+// physical index (bra = conj(P T) for Hermitian P), taking the children's
+// messages on tree legs and the converged messages elsewhere; each such
+// message is scaled to unit norm with its log norm kept in FP64; the root
+// closes its last leg against the incoming message.
+std::vector<int> steiner_edges(const HostGraph& g, std::vector<int> terms) {
+  std::sort(terms.begin(), terms.end());
+  std::vector<int> par(g.n, -2);
+  std::vector<int> q{terms[0]};
+  par[terms[0]] = -1;
+  for (size_t h0 = 0; h0 < q.size(); ++h0) {
+    const int v = q[h0];
+    for (int e : g.legs[v]) {
+      const int w = g.other(e, v);
+      if (par[w] == -2) { par[w] = e; q.push_back(w); }
+    }
+  }
+  std::vector<char> used(g.eu.size(), 0);
+  for (size_t i = 1; i < terms.size(); ++i)
+    for (int v = terms[i]; par[v] >= 0; v = g.other(par[v], v)) used[par[v]] = 1;
+  std::vector<int> out;
+  for (int e = 0; e < (int)used.size(); ++e)
+    if (used[e]) out.push_back(e);
+  return out;
+}
+
+// Run a plan built at call time; its pointer arrays go to `arena` first.
+tn_status run_adhoc(tn_handle* h, Plan& P, void* arena) {
+  std::vector<const void*> host;
+  for (auto& L : P.L) {
+    for (auto q : L.A) host.push_back(q);
+    for (auto q : L.B) host.push_back(q);
+    for (auto q : L.C) host.push_back(q);
+  }
+  TN_CUDA_TRY(cudaMemcpyAsync(arena, host.data(), host.size() * sizeof(void*),
+                              cudaMemcpyHostToDevice, h->stream));
+  const void** base = (const void**)arena;
+  size_t pos = 0;
+  for (auto& L : P.L) {
+    L.d.A = (const float* const*)(base + pos); pos += L.A.size();
+    L.d.B = (const float* const*)(base + pos); pos += L.B.size();
+    L.d.C = (float* const*)(base + pos); pos += L.C.size();
+  }
+  return run_plan(h, P, P_RHO);
+}
+
+// <value> = (scalar, log scale) of the tree contraction with operator letters
+// op[v] ('X', 'Y', 'Z', or 0 for the identity) on the tree's sites.
+tn_status region_contract(tn_handle* h, const std::vector<int>& tree, const std::vector<char>& op,
+                          double* re, double* im, double* logscale, bool* zero) {
+  const HostGraph& g = h->g;
+  const int x = h->chi;
+  const int64_t c2 = (int64_t)x * x;
+  std::vector<int> eidx(g.eu.size(), -1);
+  for (size_t i = 0; i < tree.size(); ++i) eidx[tree[i]] = (int)i;
+  int root = g.n;
+  for (int e : tree) root = std::min(root, std::min(g.eu[e], g.ew[e]));
+  // depth-first order from the root along tree edges; parent edge per site
+  std::vector<int> order, parent(g.n, -2);
+  {
+    std::vector<int> stack{root};
+    parent[root] = -1;
+    while (!stack.empty()) {
+      const int v = stack.back();
+      stack.pop_back();
+      order.push_back(v);
+      for (int e : g.legs[v]) {
+        if (eidx[e] < 0) continue;
+        const int w = g.other(e, v);
+        if (parent[w] == -2) { parent[w] = e; stack.push_back(w); }
+      }
+    }
+  }
+  // operator sites: bra copies P T and their first-leg-last copies
+  std::vector<int> opsites;
+  std::vector<int64_t> op_off;
+  int64_t bra_floats = 0;
+  for (int v : order)
+    if (op[v]) { opsites.push_back(v); op_off.push_back(bra_floats); bra_floats += 4 * h->t_len[v]; }
+  const size_t n_te = tree.size();
+  const size_t n_ptr = 9 * order.size() + 16;
+  const size_t bytes = sizeof(float) * (n_te * 6 * c2 + 2 * c2 + 2 * bra_floats) +
+                       sizeof(int64_t) * (op_off.size() + 1) + sizeof(void*) * n_ptr + 64;
+  unsigned char* buf = (unsigned char*)dev_alloc(h, bytes);
+  if (!buf) { set_error("device allocation for the region contraction failed"); return TN_ENOMEM; }
+  float* up = (float*)buf;                        // [n_te][2 c2] messages child -> parent
+  float* upr = up + n_te * 2 * c2;                // [n_te][4 c2] realified transposed
+  float* root_out = upr + n_te * 4 * c2;          // [2 c2]
+  float* bra = root_out + 2 * c2;                 // operator copies
+  float* braA = bra + bra_floats;
+  int64_t* d_off = (int64_t*)(braA + bra_floats);
+  void* arena = (void*)(((uintptr_t)(d_off + op_off.size() + 1) + 15) & ~uintptr_t(15));
+  double* scal = (double*)((unsigned char*)arena + sizeof(void*) * n_ptr);  // re, im, log
+  int* zflag = (int*)(scal + 3);
+  tn_status st = TN_OK;
+  auto fail_free = [&](tn_status code) { cudaStreamSynchronize(h->stream); dev_free(h, buf); return code; };
+  if (!op_off.empty())
+    if (cudaMemcpyAsync(d_off, op_off.data(), sizeof(int64_t) * op_off.size(),
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return fail_free(TN_ECUDA);
+  for (size_t k = 0; k < opsites.size(); ++k) {
+    const int v = opsites[k];
+    const int64_t len = h->t_len[v];
+    if (cudaMemcpyAsync(bra + op_off[k], site_ptr(h, h->T, v), sizeof(float) * 4 * len,
+                        cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return fail_free(TN_ECUDA);
+    // Pauli on p: u = [[u00, u01], [u10, u11]] as (re, im) pairs
+    float u[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (op[v] == 'X') { u[2] = 1; u[4] = 1; }
+    else if (op[v] == 'Y') { u[3] = -1; u[5] = 1; }
+    else { u[0] = 1; u[6] = -1; }
+    if (launch_phys_gate(bra, d_off + k, 1, len, 2 * len, u[0], u[1], u[2], u[3], u[4], u[5],
+                         u[6], u[7], h->stream) != cudaSuccess)
+      return fail_free(TN_ECUDA);
+    const int d = g.degree(v);
+    if (d >= 2 && launch_first_leg_last(bra, braA, d_off + k, 1, d, x, h->stream) != cudaSuccess)
+      return fail_free(TN_ECUDA);
+  }
+  if (cudaMemsetAsync(scal, 0, 3 * sizeof(double) + sizeof(int), h->stream) != cudaSuccess)
+    return fail_free(TN_ECUDA);
+  for (auto it = order.rbegin(); it != order.rend() && st == TN_OK; ++it) {
+    const int v = *it;
+    const auto& lg = g.legs[v];
+    const int d = (int)lg.size();
+    const bool is_root = parent[v] == -1;
+    float* out = is_root ? root_out : up + eidx[parent[v]] * 2 * c2;
+    ChainSite c = handle_site(h, v, out);
+    for (size_t k = 0; k < opsites.size(); ++k)
+      if (opsites[k] == v) { c.bra = bra + op_off[k]; c.braA = braA + op_off[k]; }
+    for (int j = 0; j < d; ++j)
+      if (eidx[lg[j]] >= 0 && lg[j] != parent[v]) c.m[j] = upr + eidx[lg[j]] * 4 * c2;
+    const int open = is_root ? 0 : g.leg_pos(v, parent[v]);
+    Plan P;
+    if (d == 3) deg3_chain_sites(h, P, open, {c}, false);
+    else if (d == 2) deg2_chain_sites(h, P, open, {c}, false);
+    else add_close(P, 1, 0, x, false, h->cfg.prec, {{c.T, c.bra, out}});
+    st = run_adhoc(h, P, arena);
+    if (st) break;
+    if (!is_root) {
+      if (launch_scale_unit(out, x, scal + 2, zflag, h->stream) != cudaSuccess ||
+          launch_realify(out, 2 * c2, upr + eidx[parent[v]] * 4 * c2, 1, x, h->stream) != cudaSuccess)
+        st = TN_ECUDA;
+    } else {
+      const int e = lg[0];
+      const float* m_in = eidx[e] >= 0 ? up + eidx[e] * 2 * c2
+                                       : msg_ptr(h, h->msg, dir_id(g, g.other(e, v), e));
+      if (launch_dot_msgs(root_out, m_in, x, scal, h->stream) != cudaSuccess) st = TN_ECUDA;
+    }
+  }
+  double hs[4] = {0, 0, 0, 0};
+  if (st == TN_OK &&
+      (cudaMemcpyAsync(hs, scal, 3 * sizeof(double) + sizeof(int), cudaMemcpyDeviceToHost,
+                       h->stream) != cudaSuccess ||
+       cudaStreamSynchronize(h->stream) != cudaSuccess))
+    st = TN_ECUDA;
+  if (st) return fail_free(st);
+  dev_free(h, buf);
+  *re = hs[0];
+  *im = hs[1];
+  *logscale = hs[2];
+  int zf = 0;
+  memcpy(&zf, &hs[3], sizeof(int));
+  *zero = zf != 0;
+  return TN_OK;
+}
+
+tn_status region_expectation(tn_handle* h, const tn_pauli& P, double* out) {
+  std::vector<int> terms(P.sites, P.sites + P.weight);
+  const std::vector<int> tree = steiner_edges(h->g, terms);
+  std::vector<char> op(h->g.n, 0), none(h->g.n, 0);
+  for (int j = 0; j < P.weight; ++j) op[P.sites[j]] = P.paulis[j];
+  tn_status st = ensure_ta(h);
+  if (st) return st;
+  st = ensure_mrt(h);
+  if (st) return st;
+  double nr, ni, nl, dr, di, dl;
+  bool nz, dz;
+  st = region_contract(h, tree, op, &nr, &ni, &nl, &nz);
+  if (st) return st;
+  st = region_contract(h, tree, none, &dr, &di, &dl, &dz);
+  if (st) return st;
+  if (dz || !(dr * dr + di * di > 0.0)) {
+    set_error("the region's norm contraction vanished");
+    return TN_ENUMERIC;
+  }
+  if (nz) { *out = 0.0; return TN_OK; }
+  // (n / d) exp(nl - dl), real part (P is Hermitian)
+  const double den = dr * dr + di * di;
+  *out = (nr * dr + ni * di) / den * exp(nl - dl);
+  return TN_OK;
+}
+
 tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t method,
                     double* out) {
   if (!h || (!ops && n_ops > 0) || (!out && n_ops > 0)) { set_error("null argument"); return TN_EINVAL; }
@@ -1512,8 +1756,11 @@ tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t me
       continue;
     }
     if (method == 0) {
-      set_error("region contraction of strings of weight > 1 is not built yet");
-      return TN_EUNSUPPORTED;
+      double v = 0.0;
+      tn_status st = region_expectation(h, P, &v);
+      if (st) return st;
+      out[i] = sgn * v;
+      continue;
     }
     PauliString s;
     s.ops.assign(n, 0);

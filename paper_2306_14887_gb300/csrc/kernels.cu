@@ -344,6 +344,40 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
   }
 }
 
+// Region contractions: an up-message scaled to unit Frobenius norm, its log
+// norm added to *logacc (one CTA, launches in stream order: a fixed summation
+// order); a zero message sets *zero instead.
+__global__ void scale_unit_kernel(float* m, int chi, double* logacc, int* zero) {
+  __shared__ double sh[32];
+  const int n2 = chi * chi;
+  float s0 = 0.f, c0 = 0.f;
+  for (int i = threadIdx.x; i < 2 * n2; i += blockDim.x) pair_add_sq(s0, c0, m[i]);
+  const double ss = block_sum((double)s0 + (double)c0, sh);
+  const double nrm = sqrt(ss);
+  if (!(nrm > 0.0) || !isfinite(nrm)) {
+    if (threadIdx.x == 0) *zero = 1;
+    return;
+  }
+  const float inv = (float)(1.0 / nrm);
+  for (int i = threadIdx.x; i < 2 * n2; i += blockDim.x) m[i] *= inv;
+  if (threadIdx.x == 0) *logacc += log(nrm);
+}
+
+// out = sum_ij R[i][j] M[i][j] (planar complex chi x chi), FP64.
+__global__ void dot_msgs_kernel(const float* R, const float* M, int chi, double* out) {
+  __shared__ double sh[32];
+  const int n2 = chi * chi;
+  double re = 0.0, im = 0.0;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    const double ar = R[i], ai = R[n2 + i], br = M[i], bi = M[n2 + i];
+    re += ar * br - ai * bi;
+    im += ar * bi + ai * br;
+  }
+  re = block_sum(re, sh);
+  im = block_sum(im, sh);
+  if (threadIdx.x == 0) { out[0] = re; out[1] = im; }
+}
+
 // Realified transposed copies (see GemmDesc::b_pre).
 __global__ void realify_kernel(const float* src, int64_t stride, float* dst, int chi) {
   const int64_t n2 = (int64_t)chi * chi;
@@ -387,6 +421,16 @@ __global__ void first_leg_last_kernel(const float* T, float* TA, const int64_t* 
   }
 }
 }  // namespace
+
+cudaError_t launch_scale_unit(float* m, int chi, double* logacc, int* zero, cudaStream_t s) {
+  scale_unit_kernel<<<1, 256, 0, s>>>(m, chi, logacc, zero);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_msgs(const float* R, const float* M, int chi, double* out, cudaStream_t s) {
+  dot_msgs_kernel<<<1, 256, 0, s>>>(R, M, chi, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_realify(const float* src, int64_t src_stride, float* dst, int n, int chi,
                            cudaStream_t s) {
