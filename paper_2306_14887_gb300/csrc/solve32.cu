@@ -419,10 +419,21 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
         if (lane == 0) s.nrm[j] = acc;
       }
       __syncthreads();
+      // rows taken in order of decreasing norm this sweep (ties by index)
+      for (int i = tid; i < n; i += blockDim.x) {
+        const float ni = s.nrm[i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+          const float nj = s.nrm[j];
+          rk += (nj > ni) || (nj == ni && j < i);
+        }
+        s.order[rk] = i;
+      }
+      __syncthreads();
       int any = 0;
       for (int B = half; B >= 1; B >>= 1) {
         const int g = slot / B, i = slot - g * B;
-        const int prow = g * 2 * B + i;
+        const int prow = s.order[g * 2 * B + i];
         float4 xs[4];
         float al = 0.f;
         if (active) {
@@ -434,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
         for (int r = 0; r < B; ++r) {
           int rot = 0;
           if (active) {
-            const int q = g * 2 * B + B + (i + r) % B;
+            const int q = s.order[g * 2 * B + B + (i + r) % B];
             float4 xq[4];
             float gr = 0.f, gi = 0.f;
 #pragma unroll
