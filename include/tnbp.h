@@ -313,6 +313,19 @@ tn_status tn_truncation_solve_noalloc(const float* gram, float* dmat, double* s_
                                       int32_t n_edges, int32_t chi, int32_t sign,
                                       double svd_cutoff, void* cuda_stream);
 
+/*
+ * tn_bond_spectrum — the chi normalised singular values (descending, zero
+ * padded, sum of squares 1) that the truncation solve kept on edge e at the
+ * edge's last gate (Methods, "The simple update procedure"); the product
+ * state's (1, 0, .., 0) before any gate.  out: chi host doubles.
+ * tn_entanglement_entropy — s = -sum_i lambda_i^2 log2 lambda_i^2 over that
+ * spectrum: the entanglement entropy across the edge in the BP-gauged state
+ * (Eq. EntanglementEntropy of "Dynamics of the infinite heavy-hex lattice",
+ * read with the minus sign the printed formula lacks).  Errors: TN_EINVAL.
+ */
+tn_status tn_bond_spectrum(tn_handle* h, int32_t e, double* out);
+tn_status tn_entanglement_entropy(tn_handle* h, int32_t e, double* out);
+
 /* tn_get_stats — counters of the last evolution call. */
 tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
 

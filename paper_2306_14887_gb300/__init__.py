@@ -32,7 +32,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_profile_read", "tn_profile_class_name", "tn_truncation_solve",
            "tn_truncation_solve_noalloc", "tn_truncation_solve_ex", "tn_last_error",
            "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
-           "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy"]
+           "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
+           "tn_bond_spectrum", "tn_entanglement_entropy"]
 
 
 class TNError(RuntimeError):
@@ -142,6 +143,8 @@ def lib():
         L.tn_truncation_solve_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, vp]
         L.tn_truncation_solve_ex.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, i32, vp]
         L.tn_apply_floquet_field.argtypes = [vp, dp, i32]
+        L.tn_bond_spectrum.argtypes = [vp, i32, dp]
+        L.tn_entanglement_entropy.argtypes = [vp, i32, dp]
         L.tn_server_create.argtypes = [C.POINTER(tn_server_config), C.POINTER(vp)]
         L.tn_server_submit.argtypes = [vp, C.POINTER(tn_job), C.POINTER(C.c_uint64)]
         L.tn_server_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(tn_result)]
@@ -358,6 +361,16 @@ class TNState:
         _check(lib().tn_expect(self._h, arr, len(strings), int(method),
                                out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
+
+    def bond_spectrum(self, e):
+        out = np.zeros(self.chi, dtype=np.float64)
+        _check(lib().tn_bond_spectrum(self._h, int(e), out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def entanglement_entropy(self, e):
+        out = C.c_double()
+        _check(lib().tn_entanglement_entropy(self._h, int(e), C.byref(out)))
+        return out.value
 
     def stats(self):
         s = tn_stats()

@@ -95,6 +95,9 @@ struct tn_handle {
   bool ta_valid = false, mrt_valid = false;
   double* work = nullptr;
   double* solve_stats = nullptr;
+  double* spectra = nullptr;          // [edges in layer order][chi] last kept bond spectra
+  std::vector<int64_t> spec_off;      // per layer: first row of its edges in spectra
+  std::vector<int> spec_row;          // per edge: its row in spectra
   int32_t* msg_vw = nullptr;      // per layer slot: directed ids of v->w and w->v
   std::vector<std::vector<int32_t>> layer_msg_vw;  // host copy per layer
   std::vector<int32_t*> d_layer_msg_vw;
@@ -924,7 +927,7 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   a.stats = h->solve_stats;
   a.flags = h->flags;
   a.max_sweeps = 30;
-  a.s_out = nullptr;
+  a.s_out = h->spectra + h->spec_off[li] * h->chi;
   {
     const int pi = prof_begin(h, P_SOLVE);
     if (use_shared_solve(h)) {
@@ -1138,7 +1141,15 @@ tn_status init_state(tn_handle* h) {
   for (int m = 0; m < nmsg; ++m)
     TN_CUDA_TRY(cudaMemcpyAsync(h->msg + (int64_t)m * 2 * c2, &one, sizeof(float),
                                 cudaMemcpyHostToDevice, h->stream));
-  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  {
+    // bond spectra of the product state: (1, 0, .., 0) on every edge
+    std::vector<double> sp(h->g.eu.size() * (size_t)h->chi, 0.0);
+    for (size_t e = 0; e < h->g.eu.size(); ++e) sp[e * h->chi] = 1.0;
+    if (!sp.empty())
+      TN_CUDA_TRY(cudaMemcpyAsync(h->spectra, sp.data(), sizeof(double) * sp.size(),
+                                  cudaMemcpyHostToDevice, h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
   h->ta_valid = false;
   h->mrt_valid = false;
   return TN_OK;
@@ -1157,6 +1168,7 @@ size_t footprint_of(const HostGraph& g, int chi) {
   b += 2 * sizeof(float) * (size_t)(2 * g.eu.size()) * 2 * c2;  // msg, raw
   b += 2 * sizeof(float) * maxl * 8 * c2;                  // gram, dmat
   b += sizeof(double) * maxl * solve_work_doubles(chi);    // work
+  b += sizeof(double) * g.eu.size() * (size_t)chi;        // bond spectra
   return b;
 }
 
@@ -1288,6 +1300,15 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->drt = (float*)dev_alloc(h, sizeof(float) * h->max_layer * 16 * c2);
   h->work = (double*)dev_alloc(h, sizeof(double) * h->max_layer * solve_work_doubles(chi));
   h->solve_stats = (double*)dev_alloc(h, sizeof(double) * 4 * h->max_layer);
+  h->spectra = (double*)dev_alloc(h, sizeof(double) * std::max<size_t>(1, g.eu.size()) * chi);
+  {
+    h->spec_row.assign(g.eu.size(), 0);
+    int64_t row = 0;
+    for (const auto& layer : g.layers) {
+      h->spec_off.push_back(row);
+      for (int e : layer) h->spec_row[e] = (int)row++;
+    }
+  }
   h->res_bits = (unsigned long long*)dev_alloc(h, 64);
   h->flags = h->res_bits ? reinterpret_cast<int*>(h->res_bits + 1) : nullptr;
   h->rho = (double*)dev_alloc(h, sizeof(double) * 8 * g.n);
@@ -1310,7 +1331,8 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->TA || !h->mrt || !h->drt || !h->msg ||
       !h->raw || !h->gram || !h->dmat ||
-      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho || !h->rx_cs) {
+      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho || !h->rx_cs ||
+      !h->spectra) {
     set_error("device allocation failed (footprint " + std::to_string(footprint_of(g, chi)) +
               " bytes)");
     return fail(TN_ENOMEM);
@@ -1785,6 +1807,29 @@ tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t me
     out[i] = sgn * zs * pauli_from_rho(&r2[8 * site], 'Z');
   }
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status tn_bond_spectrum(tn_handle* h, int32_t e, double* out) {
+  if (!h || !out) { set_error("null argument"); return TN_EINVAL; }
+  if (e < 0 || e >= (int32_t)h->g.eu.size()) { set_error("edge out of range"); return TN_EINVAL; }
+  TN_CUDA_TRY(cudaMemcpyAsync(out, h->spectra + (int64_t)h->spec_row[e] * h->chi,
+                              sizeof(double) * h->chi, cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status tn_entanglement_entropy(tn_handle* h, int32_t e, double* out) {
+  if (!out) { set_error("null argument"); return TN_EINVAL; }
+  std::vector<double> sp(h ? h->chi : 0);
+  tn_status st = tn_bond_spectrum(h, e, sp.data());
+  if (st) return st;
+  double s = 0.0;
+  for (double l : sp) {
+    const double p = l * l;
+    if (p > 0.0) s -= p * std::log2(p);
+  }
+  *out = s;
   return TN_OK;
 }
 
