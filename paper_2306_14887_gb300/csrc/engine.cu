@@ -308,7 +308,7 @@ tn_status upload_plans(tn_handle* h) {
   if (h->cfg.prec == TN_TF32 && h->cfg.kernels == TN_KERNELS_AUTO) {
     size_t mbytes = 0;
     for (Plan* p : plans)
-      for (auto& L : p->L) mbytes += tc_stream_map_bytes((int)L.A.size());
+      for (auto& L : p->L) mbytes += tc_stream_map_bytes((int)L.A.size() * L.d.n_inner);
     std::vector<unsigned char> hm(mbytes + 64);
     unsigned char* base =
         (unsigned char*)(((uintptr_t)hm.data() + 63) & ~uintptr_t(63));
@@ -324,7 +324,7 @@ tn_status upload_plans(tn_handle* h) {
           L.sp = sp;
           users.push_back(&L);
           offs.push_back(mpos);
-          mpos += tc_stream_map_bytes((int)L.A.size());
+          mpos += tc_stream_map_bytes(sp.n_outer);
         }
       }
     if (mpos > 0) {

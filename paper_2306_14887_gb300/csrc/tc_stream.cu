@@ -601,8 +601,10 @@ cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err,
 bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
                      size_t part_floats, void* host_maps, TcStreamPlan* p) {
   if (d.prec != TN_TF32 || d.b_pre || d.M != 64 || d.N != 64 || d.a_k2 != 1 || d.b_k2 != 1 ||
-      d.n_inner != 1 || d.K2 % 32 || d.M2 > 1 || d.M3 > 1 || d.accumulate || n_outer < 1)
+      d.n_inner < 1 || d.K2 % 32 || d.M2 > 1 || d.M3 > 1 || d.accumulate || n_outer < 1)
     return false;
+  // entries (outer, inner) in the order the partial buffer and the reduce use
+  const int n_ent = n_outer * d.n_inner;
   if (tc_stream_prepare() != cudaSuccess) return false;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
@@ -612,32 +614,36 @@ bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* cons
     if (s_a[i] <= 0 || s_b[i] <= 0 || (s_a[i] * 4) % 16 || (s_b[i] * 4) % 16) return false;
   const int chunks = d.K1 * d.K2 / 32;
   int S = 1;
-  while ((int64_t)n_outer * S * 2 <= 2LL * g_num_sms && chunks / (S * 2) >= 4) S *= 2;
+  while ((int64_t)n_ent * S * 2 <= 2LL * g_num_sms && chunks / (S * 2) >= 4) S *= 2;
   const int per = (chunks + S - 1) / S;
   S = (chunks + per - 1) / per;  // every split holds at least one chunk
-  if ((size_t)S * n_outer * 2 * 4096 > part_floats) return false;
+  if ((size_t)S * n_ent * 2 * 4096 > part_floats) return false;
   CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host_maps);
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const cuuint32_t box[4] = {32, 64, 1, 2};
-  for (int e = 0; e < n_outer; ++e) {
-    if ((reinterpret_cast<uintptr_t>(A[e]) & 15) || (reinterpret_cast<uintptr_t>(B[e]) & 15))
+  if ((d.a_in * 4) % 16 || (d.b_in * 4) % 16) return false;
+  for (int e = 0; e < n_ent; ++e) {
+    const int o = e / d.n_inner, in = e - o * d.n_inner;
+    const float* Ae = A[o] + (int64_t)in * d.a_in;
+    const float* Be = B[o] + (int64_t)in * d.b_in;
+    if ((reinterpret_cast<uintptr_t>(Ae) & 15) || (reinterpret_cast<uintptr_t>(Be) & 15))
       return false;
     cuuint64_t dims[4] = {(cuuint64_t)d.K2, 64, (cuuint64_t)d.K1, 2};
     cuuint64_t sa[3] = {(cuuint64_t)(s_a[0] * 4), (cuuint64_t)(s_a[1] * 4),
                         (cuuint64_t)(s_a[2] * 4)};
     cuuint64_t sb[3] = {(cuuint64_t)(s_b[0] * 4), (cuuint64_t)(s_b[1] * 4),
                         (cuuint64_t)(s_b[2] * 4)};
-    if (enc(&maps[e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(A[e]), dims, sa, box,
+    if (enc(&maps[e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(Ae), dims, sa, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
-    if (enc(&maps[n_outer + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(B[e]), dims,
+    if (enc(&maps[n_ent + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(Be), dims,
             sb, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
   p->kind = 1;
-  p->n_outer = n_outer;
+  p->n_outer = n_ent;  // entries: outer x inner
   p->splits = S;
   p->rank = 4;
   return true;
