@@ -143,9 +143,10 @@ cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site
 
 // rho[site][p][p'] = sum_r X[p][r] conj(T[p'][r]) in FP64 (complex, 8 doubles
 // per site).  x_off / t_off: real-plane offsets; len = chi^d; plane = 2*len.
+// rho of n_sites sites; part: scratch of n_sites * 16 * 8 doubles.
 cudaError_t launch_rho(const float* X, const float* T, const int64_t* x_off,
                        const int64_t* t_off, int n_sites, int64_t len, int64_t plane,
-                       double* rho, cudaStream_t s);
+                       double* rho, double* part, cudaStream_t s);
 
 // Batched copy of equally sized blocks: dst[i][0..n) = src[i][0..n).
 cudaError_t launch_copy_blocks(float* const* dst, const float* const* src, int n_blocks,

@@ -105,6 +105,7 @@ struct tn_handle {
   unsigned long long* res_bits = nullptr;
   int* flags = nullptr;
   double* rho = nullptr;
+  double* rho_part = nullptr;  // [site][block][8] partial sums of rho
   int64_t* site_offs_by_deg[4] = {nullptr, nullptr, nullptr, nullptr};
   float2* rx_cs = nullptr;   // per-site (cos, sin) of theta_v / 2, by degree blocks
   int rx_base[4] = {0, 0, 0, 0};
@@ -1102,9 +1103,9 @@ tn_status compute_rho(tn_handle* h, std::vector<double>* rho_out) {
     const int64_t len = ipow(h->chi, r.deg);
     const int pi = prof_begin(h, P_RHO);
     TN_CUDA_TRY(launch_rho(h->Y1, h->T, r.d_x, r.d_t, (int)r.sites.size(), len, 2 * len,
-                           h->rho + 8 * base, h->stream));
+                           h->rho + 8 * base, h->rho_part, h->stream));
     prof_end(h, pi, 32.0 * len * r.sites.size(), 2.0 * 16.0 * len * r.sites.size());
-    h->stats.kernel_launches++;
+    h->stats.kernel_launches += 2;
     for (int v : r.sites) order.push_back(v);
     base += (int)r.sites.size();
   }
@@ -1312,6 +1313,7 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->res_bits = (unsigned long long*)dev_alloc(h, 64);
   h->flags = h->res_bits ? reinterpret_cast<int*>(h->res_bits + 1) : nullptr;
   h->rho = (double*)dev_alloc(h, sizeof(double) * 8 * g.n);
+  h->rho_part = (double*)dev_alloc(h, sizeof(double) * 16 * 8 * std::max(1, g.n));
   for (int d = 1, base = 0; d <= 3; ++d) {
     h->n_by_deg[d] = (int)h->sites_by_deg[d].size();
     h->site_offs_by_deg[d] = (int64_t*)dev_alloc(h, sizeof(int64_t) * (h->n_by_deg[d] + 1));
@@ -1331,7 +1333,8 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->TA || !h->mrt || !h->drt || !h->msg ||
       !h->raw || !h->gram || !h->dmat ||
-      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho || !h->rx_cs ||
+      !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho || !h->rho_part ||
+      !h->rx_cs ||
       !h->spectra) {
     set_error("device allocation failed (footprint " + std::to_string(footprint_of(g, chi)) +
               " bytes)");

@@ -488,33 +488,73 @@ cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
 // rho[p][p'] = sum_r X[p][r] conj(T[p'][r]), FP64 accumulation, one CTA per site.
 // ---------------------------------------------------------------------------
 namespace {
-__global__ void rho_kernel(const float* X, const float* T, const int64_t* x_off,
-                           const int64_t* t_off, int64_t len, int64_t plane, double* rho) {
+// s + c += a b without rounding loss (exact product split by FMA, two-sum).
+__device__ __forceinline__ void pair_add_prod(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  c += (__fsub_rn(s, __fsub_rn(t, bp)) + __fsub_rn(p, bp)) + e;
+  s = t;
+}
+
+// rho_v[p][q] = sum_i X_v[p][i] conj(T_v[q][i]): grid (blocks per site, sites);
+// each thread keeps the 8 real parts as compensated FP32 pairs (about 48 bits,
+// off the FP64 pipe), each CTA writes its 8 sums to part[site][block][8]; a
+// second kernel adds the blocks in a fixed order in FP64.
+__global__ void rho_part_kernel(const float* X, const float* T, const int64_t* x_off,
+                                const int64_t* t_off, int64_t len, int64_t plane, double* part) {
   __shared__ double sh[32];
-  const float* x = X + x_off[blockIdx.x];
-  const float* t = T + t_off[blockIdx.x];
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-    const double x0r = x[i], x0i = x[plane + i], x1r = x[len + i], x1i = x[plane + len + i];
-    const double t0r = t[i], t0i = t[plane + i], t1r = t[len + i], t1i = t[plane + len + i];
-    // x_p * conj(t_q)
-    acc[0] += x0r * t0r + x0i * t0i;  acc[1] += x0i * t0r - x0r * t0i;   // (0,0)
-    acc[2] += x0r * t1r + x0i * t1i;  acc[3] += x0i * t1r - x0r * t1i;   // (0,1)
-    acc[4] += x1r * t0r + x1i * t0i;  acc[5] += x1i * t0r - x1r * t0i;   // (1,0)
-    acc[6] += x1r * t1r + x1i * t1i;  acc[7] += x1i * t1r - x1r * t1i;   // (1,1)
+  const float* x = X + x_off[blockIdx.y];
+  const float* t = T + t_off[blockIdx.y];
+  float s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x0r = x[i], x0i = x[plane + i], x1r = x[len + i], x1i = x[plane + len + i];
+    const float t0r = t[i], t0i = t[plane + i], t1r = t[len + i], t1i = t[plane + len + i];
+    // x_p conj(t_q) = (xr tr + xi ti) + i (xi tr - xr ti)
+    pair_add_prod(s[0], c[0], x0r, t0r); pair_add_prod(s[0], c[0], x0i, t0i);
+    pair_add_prod(s[1], c[1], x0i, t0r); pair_add_prod(s[1], c[1], -x0r, t0i);
+    pair_add_prod(s[2], c[2], x0r, t1r); pair_add_prod(s[2], c[2], x0i, t1i);
+    pair_add_prod(s[3], c[3], x0i, t1r); pair_add_prod(s[3], c[3], -x0r, t1i);
+    pair_add_prod(s[4], c[4], x1r, t0r); pair_add_prod(s[4], c[4], x1i, t0i);
+    pair_add_prod(s[5], c[5], x1i, t0r); pair_add_prod(s[5], c[5], -x1r, t0i);
+    pair_add_prod(s[6], c[6], x1r, t1r); pair_add_prod(s[6], c[6], x1i, t1i);
+    pair_add_prod(s[7], c[7], x1i, t1r); pair_add_prod(s[7], c[7], -x1r, t1i);
   }
-  for (int c = 0; c < 8; ++c) {
-    const double s = block_sum(acc[c], sh);
-    if (threadIdx.x == 0) rho[blockIdx.x * 8 + c] = s;
+  for (int k = 0; k < 8; ++k) {
+    const double v = block_sum((double)s[k] + (double)c[k], sh);
+    if (threadIdx.x == 0) part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + k] = v;
   }
+}
+
+__global__ void rho_sum_kernel(const double* part, int nblk, int n_sites, double* rho) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (site, component)
+  if (i >= 8 * n_sites) return;
+  const int site = i / 8, k = i % 8;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += part[((int64_t)site * nblk + b) * 8 + k];
+  rho[i] = v;
 }
 }  // namespace
 
+int rho_blocks(int n_sites, int64_t len) {
+  int nblk = (2 * 152 + n_sites - 1) / n_sites;
+  const int64_t most = (len + 255) / 256;
+  if (nblk > most) nblk = (int)most;
+  if (nblk > 16) nblk = 16;
+  return nblk < 1 ? 1 : nblk;
+}
+
 cudaError_t launch_rho(const float* X, const float* T, const int64_t* x_off,
                        const int64_t* t_off, int n_sites, int64_t len, int64_t plane,
-                       double* rho, cudaStream_t s) {
+                       double* rho, double* part, cudaStream_t s) {
   if (n_sites <= 0) return cudaSuccess;
-  rho_kernel<<<n_sites, 256, 0, s>>>(X, T, x_off, t_off, len, plane, rho);
+  const int nblk = rho_blocks(n_sites, len);
+  rho_part_kernel<<<dim3(nblk, n_sites), 256, 0, s>>>(X, T, x_off, t_off, len, plane, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rho_sum_kernel<<<(8 * n_sites + 255) / 256, 256, 0, s>>>(part, nblk, n_sites, rho);
   return cudaGetLastError();
 }
 
