@@ -278,26 +278,34 @@ __global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
 
 // The raw message is staged in shared memory (coalesced loads), so that the
 // transposed entry needed by the Hermitisation is a shared-memory read.
-__global__ void normalise_kernel(const float* raw, float* msg, int chi,
-                                 unsigned long long* res_bits, int* flags, float* mrt) {
+__global__ void normalise_kernel(const float* __restrict__ raw, float* __restrict__ msg, int chi,
+                                 unsigned long long* res_bits, int* flags,
+                                 float* __restrict__ mrt) {
   __shared__ double sh[32];
-  extern __shared__ float sraw[];  // re plane, im plane: chi x (chi + 1) each (padded rows)
+  // re and im planes of the new message, chi x (chi + 1) each (padded rows for
+  // the transposed reads), then the old message's two planes, chi x chi each
+  extern __shared__ float sraw[];
   const int ld = chi + 1;
   const int n2 = chi * chi;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float* sre = sraw;
   float* sim = sraw + chi * ld;
+  float* smr = sim + chi * ld;
+  float* smi = smr + n2;
   const float* r = raw + (int64_t)blockIdx.x * 2 * n2;
   float* m = msg + (int64_t)blockIdx.x * 2 * n2;
-  // rows i over warps, columns j over lanes: no index division
+  // every global read up front (coalesced, all in flight together): rows i over
+  // warps, columns j over lanes, no index division
   for (int i = warp; i < chi; i += nw)
     for (int j = lane; j < chi; j += 32) {
       sre[i * ld + j] = r[i * chi + j];
       sim[i * ld + j] = r[n2 + i * chi + j];
+      smr[i * chi + j] = m[i * chi + j];
+      smi[i * chi + j] = m[n2 + i * chi + j];
     }
   __syncthreads();
   // H = (R + R^H) / 2: element (i, j) with the transposed read from the padded
-  // tile (consecutive lanes, consecutive j: distinct banks); sums in FP64
+  // tile (consecutive lanes, consecutive j: distinct banks)
   float s0 = 0.f, c0 = 0.f;
   for (int i = warp; i < chi; i += nw)
     for (int j = lane; j < chi; j += 32) {
@@ -322,8 +330,8 @@ __global__ void normalise_kernel(const float* raw, float* msg, int chi,
       const float hr = 0.5f * (sre[i * ld + j] + sre[j * ld + i]) * inv;
       const float hi = 0.5f * (sim[i * ld + j] - sim[j * ld + i]) * inv;
       // the difference of two nearby FP32 values is exact
-      pair_add_sq(d0, dc, hr - m[idx]);
-      pair_add_sq(d0, dc, hi - m[n2 + idx]);
+      pair_add_sq(d0, dc, hr - smr[idx]);
+      pair_add_sq(d0, dc, hi - smi[idx]);
       m[idx] = hr;
       m[n2 + idx] = hi;
       if (q) {
@@ -469,7 +477,7 @@ cudaError_t normalise_prepare(int) {
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
                              unsigned long long* res_bits, int* flags, cudaStream_t s, float* mrt) {
   if (n_msgs <= 0) return cudaSuccess;
-  const size_t sm = sizeof(float) * 2 * (size_t)chi * (chi + 1);
+  const size_t sm = sizeof(float) * 2 * (size_t)chi * (chi + 1) + sizeof(float) * 2 * (size_t)chi * chi;
   if (sm > 200 * 1024) {
     normalise_gmem_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags);
     cudaError_t e = cudaGetLastError();
