@@ -428,6 +428,36 @@ __global__ void first_leg_last_kernel(const float* T, float* TA, const int64_t* 
     if (r < rest && l0 < chi) dst[r * chi + l0] = tile[tx][i];
   }
 }
+
+// The same transpose for wide slabs (rest a multiple of 128, chi of 32, site
+// offsets 16-byte aligned): a 32 x 128 tile read as 16-byte vectors (four per
+// thread in flight), written as 128-byte rows of l0.
+__global__ void first_leg_last_wide_kernel(const float* __restrict__ T, float* __restrict__ TA,
+                                           const int64_t* site_off, int chi, int64_t rest) {
+  __shared__ float tile[32][129];
+  const int site = blockIdx.z >> 2, pp = blockIdx.z & 3;
+  const int64_t len = rest * chi;
+  const float* src = T + site_off[site] + (int64_t)pp * len;  // [l0][rest]
+  float* dst = TA + site_off[site] + (int64_t)pp * len;       // [rest][l0]
+  const int64_t r0 = (int64_t)blockIdx.x * 128;
+  const int l00 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float4 v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    v[k] = *reinterpret_cast<const float4*>(src + (int64_t)(l00 + ty + 8 * k) * rest + r0 + 4 * tx);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float* row = &tile[ty + 8 * k][4 * tx];
+    row[0] = v[k].x; row[1] = v[k].y; row[2] = v[k].z; row[3] = v[k].w;
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    const int r = ty + 8 * k;
+    dst[(r0 + r) * chi + l00 + tx] = tile[tx][r];
+  }
+}
 }  // namespace
 
 cudaError_t launch_scale_unit(float* m, int chi, double* logacc, int* zero, cudaStream_t s) {
@@ -457,6 +487,15 @@ cudaError_t launch_first_leg_last(const float* T, float* TA, const int64_t* site
   int64_t rest = 1;
   for (int i = 1; i < d; ++i) rest *= chi;
   if (4LL * n_sites > 65535) return cudaErrorInvalidValue;
+  // site offsets are multiples of 4 floats (whole planes of chi^d values, chi
+  // even) when chi % 32 == 0; the base pointers come from 256-byte allocations
+  const bool wide = rest % 128 == 0 && chi % 32 == 0 &&
+                    ((reinterpret_cast<uintptr_t>(T) | reinterpret_cast<uintptr_t>(TA)) & 15) == 0;
+  if (wide) {
+    dim3 grid((unsigned)(rest / 128), (unsigned)(chi / 32), (unsigned)(4 * n_sites));
+    first_leg_last_wide_kernel<<<grid, dim3(32, 8), 0, s>>>(T, TA, site_off, chi, rest);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((rest + 31) / 32), (unsigned)((chi + 31) / 32), (unsigned)(4 * n_sites));
   first_leg_last_kernel<<<grid, dim3(32, 8), 0, s>>>(T, TA, site_off, chi, rest);
   return cudaGetLastError();
