@@ -326,6 +326,20 @@ tn_status tn_truncation_solve_noalloc(const float* gram, float* dmat, double* s_
 tn_status tn_bond_spectrum(tn_handle* h, int32_t e, double* out);
 tn_status tn_entanglement_entropy(tn_handle* h, int32_t e, double* out);
 
+/*
+ * Checkpoint / resume of a job's state: the site tensors, the messages and
+ * the bond spectra (everything later steps and expectation values read).
+ * tn_state_size gives the bytes of the host image; tn_save_state writes it
+ * into caller-owned host memory; tn_load_state restores it into a handle
+ * created with the same graph (same edges and colour layers) and chi, after
+ * which evolution continues exactly as from the saved point.  The precision
+ * and solve of the loading handle may differ.  Errors: TN_EINVAL (buffer too
+ * small, not a checkpoint, or another graph or chi), TN_ECUDA.
+ */
+tn_status tn_state_size(const tn_handle* h, size_t* bytes);
+tn_status tn_save_state(tn_handle* h, void* host, size_t bytes);
+tn_status tn_load_state(tn_handle* h, const void* host, size_t bytes);
+
 /* tn_get_stats — counters of the last evolution call. */
 tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
 

@@ -33,7 +33,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_truncation_solve_noalloc", "tn_truncation_solve_ex", "tn_last_error",
            "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
            "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
-           "tn_bond_spectrum", "tn_entanglement_entropy"]
+           "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
+           "tn_load_state"]
 
 
 class TNError(RuntimeError):
@@ -144,6 +145,9 @@ def lib():
         L.tn_truncation_solve_ex.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, i32, vp]
         L.tn_apply_floquet_field.argtypes = [vp, dp, i32]
         L.tn_bond_spectrum.argtypes = [vp, i32, dp]
+        L.tn_state_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.tn_save_state.argtypes = [vp, vp, C.c_size_t]
+        L.tn_load_state.argtypes = [vp, vp, C.c_size_t]
         L.tn_entanglement_entropy.argtypes = [vp, i32, dp]
         L.tn_server_create.argtypes = [C.POINTER(tn_server_config), C.POINTER(vp)]
         L.tn_server_submit.argtypes = [vp, C.POINTER(tn_job), C.POINTER(C.c_uint64)]
@@ -361,6 +365,18 @@ class TNState:
         _check(lib().tn_expect(self._h, arr, len(strings), int(method),
                                out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
+
+    def save_state(self):
+        """Host image (bytes) of the state: site tensors, messages, bond spectra."""
+        n = C.c_size_t()
+        _check(lib().tn_state_size(self._h, C.byref(n)))
+        buf = (C.c_ubyte * n.value)()
+        _check(lib().tn_save_state(self._h, buf, n.value))
+        return bytes(buf)
+
+    def load_state(self, image):
+        buf = (C.c_ubyte * len(image)).from_buffer_copy(image)
+        _check(lib().tn_load_state(self._h, buf, len(image)))
 
     def bond_spectrum(self, e):
         out = np.zeros(self.chi, dtype=np.float64)

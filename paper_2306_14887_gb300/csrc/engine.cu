@@ -1518,6 +1518,51 @@ tn_status tn_expect_z_all(tn_handle* h, double* out) {
   return TN_OK;
 }
 
+// ----------------------------------------------------------- checkpoints
+// Host image of a job's state: a header, the site tensors, the messages and
+// the bond spectra, all as the device holds them.
+struct CkptHeader {
+  uint64_t magic;        // "TNBPCKP1"
+  uint64_t graph_hash;   // FNV-1a over n, the edge list and the colour layers
+  int64_t n_vertices, n_edges, chi, t_floats, msg_floats, spec_doubles;
+};
+constexpr uint64_t kCkptMagic = 0x31504b4350424e54ull;
+
+uint64_t graph_hash(const HostGraph& g) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (uint64_t)((v >> (8 * b)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  mix(g.n);
+  for (size_t e = 0; e < g.eu.size(); ++e) { mix(g.eu[e]); mix(g.ew[e]); }
+  for (const auto& layer : g.layers) {
+    mix(-1);
+    for (int e : layer) mix(e);
+  }
+  return h;
+}
+
+CkptHeader ckpt_header(const tn_handle* h) {
+  CkptHeader c;
+  c.magic = kCkptMagic;
+  c.graph_hash = graph_hash(h->g);
+  c.n_vertices = h->g.n;
+  c.n_edges = (int64_t)h->g.eu.size();
+  c.chi = h->chi;
+  c.t_floats = h->t_floats;
+  c.msg_floats = 2 * c.n_edges * 2 * (int64_t)h->chi * h->chi;
+  c.spec_doubles = c.n_edges * h->chi;
+  return c;
+}
+
+size_t ckpt_bytes(const CkptHeader& c) {
+  return sizeof(CkptHeader) + sizeof(float) * (size_t)(c.t_floats + c.msg_floats) +
+         sizeof(double) * (size_t)c.spec_doubles;
+}
+
 static tn_status backup_state(tn_handle* h, bool restore) {
   const int64_t c2 = (int64_t)h->chi * h->chi;
   const size_t mb = sizeof(float) * 2 * h->g.eu.size() * 2 * c2;
@@ -1810,6 +1855,63 @@ tn_status tn_expect(tn_handle* h, const tn_pauli* ops, int32_t n_ops, int32_t me
     out[i] = sgn * zs * pauli_from_rho(&r2[8 * site], 'Z');
   }
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status tn_state_size(const tn_handle* h, size_t* bytes) {
+  if (!h || !bytes) { set_error("null argument"); return TN_EINVAL; }
+  *bytes = ckpt_bytes(ckpt_header(h));
+  return TN_OK;
+}
+
+tn_status tn_save_state(tn_handle* h, void* host, size_t bytes) {
+  if (!h || !host) { set_error("null argument"); return TN_EINVAL; }
+  const CkptHeader c = ckpt_header(h);
+  if (bytes < ckpt_bytes(c)) {
+    set_error("checkpoint buffer too small: " + std::to_string(ckpt_bytes(c)) + " bytes needed");
+    return TN_EINVAL;
+  }
+  unsigned char* p = (unsigned char*)host;
+  memcpy(p, &c, sizeof(c));
+  p += sizeof(c);
+  TN_CUDA_TRY(cudaMemcpyAsync(p, h->T, sizeof(float) * c.t_floats, cudaMemcpyDeviceToHost,
+                              h->stream));
+  p += sizeof(float) * c.t_floats;
+  TN_CUDA_TRY(cudaMemcpyAsync(p, h->msg, sizeof(float) * c.msg_floats, cudaMemcpyDeviceToHost,
+                              h->stream));
+  p += sizeof(float) * c.msg_floats;
+  TN_CUDA_TRY(cudaMemcpyAsync(p, h->spectra, sizeof(double) * c.spec_doubles,
+                              cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return TN_OK;
+}
+
+tn_status tn_load_state(tn_handle* h, const void* host, size_t bytes) {
+  if (!h || !host) { set_error("null argument"); return TN_EINVAL; }
+  const CkptHeader want = ckpt_header(h);
+  CkptHeader c;
+  if (bytes < sizeof(c)) { set_error("checkpoint too short"); return TN_EINVAL; }
+  memcpy(&c, host, sizeof(c));
+  if (c.magic != kCkptMagic) { set_error("not a checkpoint of this library"); return TN_EINVAL; }
+  if (c.graph_hash != want.graph_hash || c.n_vertices != want.n_vertices ||
+      c.n_edges != want.n_edges || c.chi != want.chi || c.t_floats != want.t_floats ||
+      c.msg_floats != want.msg_floats || c.spec_doubles != want.spec_doubles) {
+    set_error("checkpoint of another graph or chi");
+    return TN_EINVAL;
+  }
+  if (bytes < ckpt_bytes(c)) { set_error("checkpoint truncated"); return TN_EINVAL; }
+  const unsigned char* p = (const unsigned char*)host + sizeof(c);
+  TN_CUDA_TRY(cudaMemcpyAsync(h->T, p, sizeof(float) * c.t_floats, cudaMemcpyHostToDevice,
+                              h->stream));
+  p += sizeof(float) * c.t_floats;
+  TN_CUDA_TRY(cudaMemcpyAsync(h->msg, p, sizeof(float) * c.msg_floats, cudaMemcpyHostToDevice,
+                              h->stream));
+  p += sizeof(float) * c.msg_floats;
+  TN_CUDA_TRY(cudaMemcpyAsync(h->spectra, p, sizeof(double) * c.spec_doubles,
+                              cudaMemcpyHostToDevice, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->ta_valid = false;
+  h->mrt_valid = false;
   return TN_OK;
 }
 
