@@ -15,9 +15,25 @@ namespace tnbp {
 // accumulators).  Operand loads pick the thread-to-element map that makes
 // consecutive threads read consecutive addresses of whichever index of the
 // operand is contiguous.
+//
+// Summation: each 16-deep slice is summed into fresh registers and the slice
+// sums are added to the running total with an error-free two-sum whose
+// rounding errors are carried in a compensation term (Knuth's TwoSum).  The
+// contractions here run over K up to 2 chi^2 (8192 at chi = 64); a single
+// running FP32 sum would carry an error growing with K, while this keeps it
+// at the 32-term slice plus a few roundings of the total.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
+
+// s + c += b with s the rounded sum and c the accumulated rounding errors.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float b) {
+  const float t = __fadd_rn(s, b);
+  const float bb = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+  s = t;
+  c = __fadd_rn(c, e);
+}
 
 __device__ __forceinline__ int64_t koff(int k, int K2, int64_t s1, int64_t s2) {
   int k1 = k / K2;
@@ -44,11 +60,11 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
   const float sa = d.conj_a ? -1.f : 1.f;
   const float sb = d.conj_b ? -1.f : 1.f;
 
-  float accr[4][4], acci[4][4];
+  float accr[4][4], acci[4][4], cmpr[4][4], cmpi[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = cmpr[i][j] = cmpi[i][j] = 0.f;
 
   for (int k0 = 0; k0 < K; k0 += BK) {
 #pragma unroll
@@ -84,6 +100,11 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
       Bs[1][kk][nn] = im;
     }
     __syncthreads();
+    float pr[4][4], pi[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pr[i][j] = pi[i][j] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float ar[4], ai[4], br[4], bi[4];
@@ -98,14 +119,28 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          accr[i][j] = fmaf(ar[i], br[j], accr[i][j]);
-          accr[i][j] = fmaf(-ai[i], bi[j], accr[i][j]);
-          acci[i][j] = fmaf(ar[i], bi[j], acci[i][j]);
-          acci[i][j] = fmaf(ai[i], br[j], acci[i][j]);
+          pr[i][j] = fmaf(ar[i], br[j], pr[i][j]);
+          pr[i][j] = fmaf(-ai[i], bi[j], pr[i][j]);
+          pi[i][j] = fmaf(ar[i], bi[j], pi[i][j]);
+          pi[i][j] = fmaf(ai[i], br[j], pi[i][j]);
         }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        two_sum_acc(accr[i][j], cmpr[i][j], pr[i][j]);
+        two_sum_acc(acci[i][j], cmpi[i][j], pi[i][j]);
+      }
     __syncthreads();
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      accr[i][j] = __fadd_rn(accr[i][j], cmpr[i][j]);
+      acci[i][j] = __fadd_rn(acci[i][j], cmpi[i][j]);
+    }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int m = m0 + ty + 16 * i;

@@ -158,6 +158,31 @@ def test_eagle127_exact_regime_matches_lightcone(tnlib):
     s.close()
 
 
+# theta_h of the bench's sweep point: the tenth of 16 points on [0, pi/2]
+BENCH_THETA = float(np.linspace(0.0, np.pi / 2, 16)[9])
+
+
+@pytest.mark.parametrize("chi", [32, 64])
+def test_bench_configuration_exact_regime_fp32(tnlib, chi):
+    """The bench workload (127 qubits, chi = 64) for its first 5 steps in FP32.
+
+    Bonds reach at most 2^5 = 32, so nothing is truncated and BP is exact
+    (the backward light cone of one site after 5 steps holds no loop of the
+    12-site heavy-hex cells); chi = 64 also exercises the zero-padded bonds.
+    All 127 <Z_v> against the FP64 oracle, a spread of sites against the
+    light-cone statevector.
+    """
+    g = OG.eagle127()
+    s = make(tnlib, g, chi)
+    s.apply_floquet(BENCH_THETA, 5)
+    z = s.expect_z_all()
+    s.close()
+    o = OB.run(g, 32, BENCH_THETA, 5)
+    assert np.abs(z - o.all_z()).max() < Z_TOL
+    for v in (0, 6, 13, 44, 62, 113, 126):
+        assert abs(z[v] - OS.lightcone_expectation(g, BENCH_THETA, 5, {v: "Z"}).real) < Z_TOL
+
+
 @pytest.mark.parametrize("solve,tol", [("fp64", Z_TOL), ("shared", Z_TOL_SHARED)])
 def test_eagle127_truncated_matches_oracle(tnlib, solve, tol):
     """127 qubits, chi = 4 < 2^5: truncation in every gate from step 3."""

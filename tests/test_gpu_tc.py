@@ -139,3 +139,35 @@ def test_streaming_and_tile_kernels_agree_chi64_saturated(tnlib):
         z[kern] = s.expect_z_all()
         s.close()
     assert np.abs(z["auto"] - z["tile"]).max() < Z_TOL["tf32"]
+
+
+BENCH_THETA = float(np.linspace(0.0, np.pi / 2, 16)[9])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3"])
+def test_bench_configuration_exact_regime(tnlib, prec):
+    """The bench workload (127 qubits, chi = 64, TMA kernels, shared solve) for
+    its first 5 steps, where nothing is truncated and BP is exact: every <Z_v>
+    within the stated bound of the FP64 oracle."""
+    g = OG.eagle127()
+    with tnlib.TNState(g.n, g.edges, g.colours, chi=64, prec=prec) as s:
+        s.apply_floquet(BENCH_THETA, 5)
+        z = s.expect_z_all()
+        # the TMA streaming and close kernels take TF32; split precision runs
+        # in the tile kernel
+        assert (s.stats()["tma_launches"] > 0) == (prec == "tf32")
+    o = OB.run(g, 32, BENCH_THETA, 5)
+    assert np.abs(z - o.all_z()).max() < Z_TOL[prec]
+
+
+def test_bench_configuration_saturated_shared_vs_fp64_solve(tnlib):
+    """Past the exact regime (8 steps, bonds saturated at chi = 64) the oracle
+    cannot follow; the shared solve is held to the TF32 bound against the FP64
+    solve on the same TF32 contractions."""
+    g = OG.eagle127()
+    z = {}
+    for solve in ("shared", "fp64"):
+        with tnlib.TNState(g.n, g.edges, g.colours, chi=64, prec="tf32", solve=solve) as s:
+            s.apply_floquet(BENCH_THETA, 8)
+            z[solve] = s.expect_z_all()
+    assert np.abs(z["shared"] - z["fp64"]).max() < Z_TOL["tf32"]
