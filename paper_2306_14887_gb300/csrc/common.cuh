@@ -89,7 +89,8 @@ cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream
 // tensor map per batch entry, encoded on the host when a plan is uploaded.
 struct TcStreamPlan {
   const void* maps = nullptr;  // device CUtensorMap[2 * n_outer]
-  int kind = 0;                // 0: mode product (streaming), 1: close (TMA split-K)
+  int kind = 0;                // 0: mode product (streaming), 1: close (TMA split-K),
+                               // 2: two fused mode products (maps: A, Bt1, Bt2)
   int n_outer = 0, rank = 0, lev0 = 1, lev1 = 1;
   int splits = 1;              // close: K splits per entry
 };
@@ -108,6 +109,16 @@ bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* cons
                      size_t part_floats, void* host_maps, TcStreamPlan* p);
 cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* part, int* err,
                             cudaStream_t s);
+// Two consecutive mode products fused (tc_stream.cu): d1 the first (A, B1 ->
+// C1), d2 the second (A2 == C1, B2 -> its C); eligible when the second reads
+// exactly what the first writes, contracting the first's innermost row level.
+// host_maps: tc_chain_map_bytes(n_outer) bytes, 64-byte aligned.
+bool tc_chain_encode(const GemmDesc& d1, const GemmDesc& d2, const float* const* A,
+                     const float* const* B1, const float* const* A2, const float* const* B2,
+                     float* const* C1, int n_outer, void* host_maps, TcStreamPlan* p);
+size_t tc_chain_map_bytes(int n_outer);
+cudaError_t launch_tc_chain(const GemmDesc& d1, const GemmDesc& d2, const TcStreamPlan& p,
+                            int* err, cudaStream_t s);
 // Kernel attributes set once, before any launch or stream capture.
 cudaError_t tc_prepare();
 cudaError_t normalise_prepare(int chi);

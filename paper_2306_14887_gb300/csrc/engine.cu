@@ -47,7 +47,9 @@ struct HostLaunch {
   GemmDesc d;
   std::vector<const float*> A, B;
   std::vector<float*> C;
-  TcStreamPlan sp;  // maps set: the launch runs in the streaming kernel
+  TcStreamPlan sp;         // maps set: the launch runs in a TMA kernel
+  bool fuse_next = false;  // the next launch contracts this one's output (chain stages)
+  bool skip = false;       // carried out by the previous launch's fused kernel
 };
 
 struct Plan {
@@ -309,7 +311,7 @@ tn_status upload_plans(tn_handle* h) {
   if (h->cfg.prec == TN_TF32 && h->cfg.kernels == TN_KERNELS_AUTO) {
     size_t mbytes = 0;
     for (Plan* p : plans)
-      for (auto& L : p->L) mbytes += tc_stream_map_bytes((int)L.A.size() * L.d.n_inner);
+      for (auto& L : p->L) mbytes += tc_chain_map_bytes((int)L.A.size() * L.d.n_inner);
     std::vector<unsigned char> hm(mbytes + 64);
     unsigned char* base =
         (unsigned char*)(((uintptr_t)hm.data() + 63) & ~uintptr_t(63));
@@ -317,8 +319,24 @@ tn_status upload_plans(tn_handle* h) {
     std::vector<size_t> offs;
     size_t mpos = 0;
     for (Plan* p : plans)
-      for (auto& L : p->L) {
+      for (size_t li = 0; li < p->L.size(); ++li) {
+        HostLaunch& L = p->L[li];
         TcStreamPlan sp;
+        if (L.skip) continue;
+        // two chain stages in one pass: the intermediate never reaches HBM
+        if (L.fuse_next && li + 1 < p->L.size()) {
+          HostLaunch& L2 = p->L[li + 1];
+          if ((int)L2.A.size() == (int)L.A.size() &&
+              tc_chain_encode(L.d, L2.d, L.A.data(), L.B.data(), L2.A.data(), L2.B.data(),
+                              L.C.data(), (int)L.A.size(), base + mpos, &sp)) {
+            L.sp = sp;
+            L2.skip = true;
+            users.push_back(&L);
+            offs.push_back(mpos);
+            mpos += tc_chain_map_bytes(sp.n_outer);
+            continue;
+          }
+        }
         if (tc_stream_encode(L.d, L.A.data(), L.B.data(), (int)L.A.size(), base + mpos, &sp) ||
             tc_close_encode(L.d, L.A.data(), L.B.data(), (int)L.A.size(), h->part_floats,
                             base + mpos, &sp)) {
@@ -413,9 +431,27 @@ bool use_tensor_cores(const tn_handle* h) {
 }
 
 tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
-  for (auto& L : P.L) {
+  for (size_t li = 0; li < P.L.size(); ++li) {
+    const HostLaunch& L = P.L[li];
+    if (L.skip) continue;
     const int pi = prof_begin(h, cls);
     int nk = 1;
+    if (L.sp.maps && L.sp.kind == 2) {
+      // two chain stages fused: the second stage's descriptor gives the output
+      const GemmDesc& d2 = P.L[li + 1].d;
+      TN_CUDA_TRY(launch_tc_chain(L.d, d2, L.sp, h->flags, h->stream));
+      h->stats.tma_launches++;
+      if (pi >= 0) {
+        double f1, b1, f2, b2;
+        gemm_work(L.d, &f1, &b1);
+        gemm_work(d2, &f2, &b2);
+        // the intermediate is neither written nor read back
+        const double y = 8.0 * L.d.M * L.d.N * L.d.n_outer;
+        prof_end(h, pi, f1 + f2, b1 + b2 - 2.0 * y);
+      }
+      h->stats.kernel_launches += 1;
+      continue;
+    }
     // contractions too small to fill a tensor-core tile pipeline (the
     // degree-1 closes: chi^2 outputs over K = 2) run on the CUDA cores in FP32
     const double macs = (double)L.d.n_outer * L.d.n_inner * L.d.M * L.d.N * L.d.K1 * L.d.K2;
@@ -592,6 +628,7 @@ void deg3_chain_sites(tn_handle* h, Plan& P, int which, const std::vector<ChainS
     if (open_p) { sc.K1 = x; sc.n_inner = 2; sc.a_in = x2; sc.b_in = x3; sc.c_in = 2 * x2; }
   }
   add_spec(P, s1, prec, e1);
+  if (!e1.empty()) P.L.back().fuse_next = true;  // Y1 feeds only the second product
   add_spec(P, s2, prec, e2);
   add_spec(P, sc, prec, ec);
 }
@@ -1018,6 +1055,8 @@ tn_status sweep_graph(tn_handle* h, bool* use) {
       gemm_work(L.d, &f, &b);
       h->sweep_flops += f;
       h->sweep_bytes += b;
+      // a fused pair neither writes nor reads back its intermediate
+      if (L.sp.maps && L.sp.kind == 2) h->sweep_bytes -= 16.0 * L.d.M * L.d.N * L.d.n_outer;
     }
   }
   *use = true;

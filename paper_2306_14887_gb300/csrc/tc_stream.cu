@@ -31,6 +31,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "tc_common.cuh"
@@ -421,6 +422,323 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
   }
 }
 
+// ------------------------------------------------------- fused mode products
+// Two consecutive mode products of a degree-3 chain in one pass (the first two
+// message legs of Eq. MessageTensorSelfConsistency), the intermediate kept on
+// chip:
+//   Y1[(o, j)][(s, n1)] = sum_(s', k) A_s'[(o, j)][k] Bt1[(s, n1)][(s', k)]
+//   Y2[(o, n1)][(t, n2)] = sum_(s, j) Y1[(o, j)][(s, n1)] Bt2[(t, n2)][(s, j)]
+// o the rows kept by both products, j the innermost row level of the first
+// (the leg the second contracts), Bt1 / Bt2 the realified transposed messages.
+// A tile is 128 rows (o, j) of the first product = 128 / chi values of o; its
+// accumulator (TMEM, double-buffered) is read by the epilogue warps and
+// written back, transposed to rows (o, n1) and K = (s, j), into a
+// 128-byte-swizzled K-major shared-memory operand (rounded to TF32), which the
+// second MMA takes with Bt2.  The second accumulator goes to global memory as
+// in the streaming kernel.  Each realified message [[Re, Im], [-Im, Re]] is
+// held as its three distinct chi x chi blocks (the (1,1) block equals (0,0)),
+// and every MMA has N = chi.
+//   warp 0 (one thread)  TMA: Bt1 / Bt2 blocks per site, the A ring (4 slots);
+//   warp 1 (one thread)  MMA: stage 1 of each tile; stage 2 of the previous
+//                        tile as soon as its operand is complete (polled
+//                        while waiting for the ring), so neither waits on the
+//                        other's inputs;
+//   warps 2..9           two per TMEM lane quadrant, one per column half (the
+//                        re / im plane): transpose into the stage-2 operand,
+//                        then the output.
+// The stage-2 operand has one buffer: an epilogue warp writes it for tile i
+// only after it has waited for stage 2 of tile i - 1 to complete.  Every wait
+// is bounded as in the streaming kernel.
+constexpr int kFThreads = 320;
+constexpr int kFEpi = 8;
+constexpr int kFSlots = 4;
+constexpr int kFBlkChunk = 64 * 128;          // [chi <= 64 rows][32 floats]
+constexpr int kFBBytes = 3 * 2 * kFBlkChunk;  // 3 blocks x chi/32 chunks
+constexpr int kFA2Bytes = 4 * kChunk;         // 2 chi / 32 chunks of [128][32]
+constexpr int kFA2Off = 2 * kFBBytes;
+constexpr int kFRingOff = kFA2Off + kFA2Bytes;
+constexpr int kFBarOff = kFRingOff + kFSlots * kChunk;
+constexpr int kFSmemBytes = kFBarOff + 256 + 1024;
+
+struct FuseArgs {
+  const CUtensorMap* maps;  // [3 * n_outer]: A maps, Bt1 maps, Bt2 maps
+  int n_outer;
+  int tiles_per_entry;
+  int rank, lev0, lev1;
+  int* err;
+};
+
+// realified block (t, s) of a message -> stored block index
+__device__ __forceinline__ int rblock(int t, int s) { return t == s ? 0 : (t == 0 ? 1 : 2); }
+
+template <int CHI>
+__global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, FuseArgs a) {
+  constexpr int NR = 2 * CHI, KC = NR / 32, KCS = CHI / 32;
+  constexpr uint32_t kCols = 8 * CHI;  // acc1 x 2 (2 chi each), acc2 (2 chi), padding
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sB1 = smem;
+  unsigned char* sB2 = smem + kFBBytes;
+  unsigned char* sA2 = smem + kFA2Off;
+  unsigned char* sA = smem + kFRingOff;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFBarOff);
+  uint64_t* empty = full + kFSlots;
+  uint64_t* bfull = empty + kFSlots;
+  uint64_t* bempty = bfull + 1;
+  uint64_t* t1full = bempty + 1;   // [2]
+  uint64_t* t1empty = t1full + 2;  // [2]
+  uint64_t* a2full = t1empty + 2;
+  uint64_t* t2full = a2full + 1;
+  uint64_t* done = t2full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int total = a.n_outer * a.tiles_per_entry;
+  const int t_beg = (int)((int64_t)blockIdx.x * total / gridDim.x);
+  const int t_end = (int)((int64_t)(blockIdx.x + 1) * total / gridDim.x);
+
+  if (tid == 0) {
+    for (int s = 0; s < kFSlots; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(bempty, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&t1full[i], 1);
+      mbar_init(&t1empty[i], kFEpi);
+    }
+    mbar_init(a2full, kFEpi);
+    mbar_init(t2full, 1);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const CUtensorMap* amaps = a.maps;
+  const CUtensorMap* b1maps = a.maps + a.n_outer;
+  const CUtensorMap* b2maps = a.maps + 2 * a.n_outer;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- producer
+    if (lane == 0) {
+      int it = 0, cur = -1, bl = 0;
+      const uint32_t bbytes = (uint32_t)(2 * 3 * KCS * CHI * 128);
+      for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile) {
+        const int e = tile / a.tiles_per_entry;
+        const int mt = tile - e * a.tiles_per_entry;
+        if (e != cur) {
+          if (cur >= 0 && !mbar_wait(bempty, (bl - 1) & 1, a.err)) { *abort_flag = 1; break; }
+          mbar_expect_tx(bfull, bbytes);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const int t = b == 2 ? 1 : 0, s = b == 1 ? 1 : 0;
+#pragma unroll
+            for (int kk = 0; kk < KCS; ++kk) {
+              const int off = (b * 2 + kk) * kFBlkChunk;
+              tma_load_2d(smem_u32(sB1 + off), b1maps + e, s * CHI + kk * 32, t * CHI, bfull);
+              tma_load_2d(smem_u32(sB2 + off), b2maps + e, s * CHI + kk * 32, t * CHI, bfull);
+            }
+          }
+          ++bl;
+          cur = e;
+        }
+        int r = mt * 128;
+        const int r0 = r % a.lev0;
+        r /= a.lev0;
+        const int r1 = r % a.lev1;
+        const int r2 = r / a.lev1;
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < KC; ++c, ++it) {
+          const int slot = it % kFSlots;
+          if (!mbar_wait(&empty[slot], ((it / kFSlots) & 1) ^ 1, a.err)) { ok = false; break; }
+          mbar_expect_tx(&full[slot], (uint32_t)kChunk);
+          const int kr = c * 32, plane = kr / CHI, k = kr - plane * CHI;
+          const uint32_t dst = smem_u32(sA + slot * kChunk);
+          if (a.rank == 3) tma_load_3d(dst, amaps + e, k, r0, plane, &full[slot]);
+          else if (a.rank == 4) tma_load_4d(dst, amaps + e, k, r0, r1, plane, &full[slot]);
+          else tma_load_5d(dst, amaps + e, k, r0, r1, r2, plane, &full[slot]);
+        }
+        if (!ok) { *abort_flag = 1; break; }
+      }
+      // before the CTA exits, every copy issued has landed: slot s took the
+      // loads it = s, s + kFSlots, ...
+      for (int s = 0; s < kFSlots; ++s) {
+        const int n = it / kFSlots + (s < it % kFSlots ? 1 : 0);
+        if (n > 0) mbar_wait(&full[s], (n - 1) & 1, a.err);
+      }
+      if (bl > 0) mbar_wait(bfull, (bl - 1) & 1, a.err);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(2, 128, CHI);
+      const uint32_t acc2 = tmem + (uint32_t)(4 * CHI);
+      int pend = -1;  // local tile whose stage 2 is not issued yet
+      // stage 2 of local tile pend; its operand is complete
+      auto issue2 = [&]() {
+        tc_fence_after();
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+          for (int c = 0; c < KC; ++c) {
+            const int s = c / KCS, kk = c - s * KCS;
+            const uint32_t a0 = smem_u32(sA2 + c * kChunk);
+            const uint32_t b0 = smem_u32(sB2 + (rblock(t, s) * 2 + kk) * kFBlkChunk);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_issue(0, acc2 + (uint32_t)(t * CHI), sw128_desc(a0 + ks * 32),
+                        sw128_desc(b0 + ks * 32), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          }
+        mma_commit(t2full);
+        pend = -1;
+      };
+      // blocking stage 2 of the pending tile
+      auto flush2 = [&]() -> bool {
+        if (pend < 0) return true;
+        if (!mbar_wait(a2full, pend & 1, a.err)) return false;
+        issue2();
+        return true;
+      };
+      // wait for a ring slot, issuing the pending stage 2 as soon as it is ready
+      auto wait_full = [&](int slot, uint32_t par) -> bool {
+        if (pend >= 0 && mbar_try_wait(a2full, pend & 1)) issue2();
+        if (mbar_try_wait(&full[slot], par)) return true;
+        const long long t0 = clock64();
+        while (true) {
+          if (pend >= 0 && mbar_try_wait(a2full, pend & 1)) issue2();
+          if (mbar_try_wait(&full[slot], par)) return true;
+          if (clock64() - t0 > kWaitCycles) {
+            atomicOr(a.err, 2);
+            return false;
+          }
+          __nanosleep(20);
+        }
+      };
+      int it = 0, cur = -1, bl = 0, i = 0;
+      bool ok = true;
+      for (int tile = t_beg; tile < t_end && ok && !*abort_flag; ++tile, ++i) {
+        const int e = tile / a.tiles_per_entry;
+        if (e != cur) {
+          // stage 2 of the last tile of the previous entry reads its Bt2
+          if (!flush2()) { ok = false; break; }
+          if (cur >= 0) mma_commit(bempty);
+          if (!mbar_wait(bfull, bl & 1, a.err)) { ok = false; break; }
+          ++bl;
+          cur = e;
+        }
+        const int buf = i & 1;
+        if (!mbar_wait(&t1empty[buf], ((i >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t acc1 = tmem + (uint32_t)(buf * NR);
+#pragma unroll
+        for (int c = 0; c < KC; ++c, ++it) {
+          const int slot = it % kFSlots;
+          if (!wait_full(slot, (it / kFSlots) & 1)) { ok = false; break; }
+          tc_fence_after();
+          const int s = c / KCS, kk = c - s * KCS;
+          const uint32_t a0 = smem_u32(sA + slot * kChunk);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            const uint32_t b0 = smem_u32(sB1 + (rblock(t, s) * 2 + kk) * kFBlkChunk);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_issue(0, acc1 + (uint32_t)(t * CHI), sw128_desc(a0 + ks * 32),
+                        sw128_desc(b0 + ks * 32), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[slot]);
+        }
+        if (!ok) break;
+        mma_commit(&t1full[buf]);
+        // at most one stage 2 outstanding: the previous tile's goes first
+        if (!flush2()) { ok = false; break; }
+        pend = i;
+      }
+      if (ok && !*abort_flag) ok = flush2();
+      if (!ok) *abort_flag = 1;
+      mma_commit(done);
+      mbar_wait(done, 0, a.err);
+    }
+    __syncwarp();
+  } else {
+    // ----------------------------------------------- transpose and epilogue
+    const int q = warp & 3;              // TMEM lane quadrant
+    const int h = (warp - 2) >> 2;       // column half: plane s of Y1, t of Y2
+    const int row = q * 32 + lane;       // (g, j) of stage 1, (g, n1) of stage 2
+    const int g = row / CHI, j = row - g * CHI;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+    // the stage-2 operand: K index (s = h, j) -> chunk h * CHI / 32 + j / 32,
+    // column j % 32 = lane; row g * CHI + n1; the 16-byte unit of a row r is
+    // swizzled by r % 8 = n1 % 8
+    unsigned char* a2base = sA2 + (h * KCS + j / 32) * kChunk + (g * CHI) * 128 + ((lane & 3) << 2);
+    uint32_t uoff[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) uoff[u] = (uint32_t)((((lane >> 2) ^ u)) << 4);
+    int i = 0;
+    for (int tile = t_beg; tile < t_end; ++tile, ++i) {
+      if (*abort_flag) break;
+      const int e = tile / a.tiles_per_entry;
+      const int mt = tile - e * a.tiles_per_entry;
+      const int buf = i & 1;
+      if (!mbar_wait(&t1full[buf], (i >> 1) & 1, a.err)) { *abort_flag = 1; break; }
+      tc_fence_after();
+      __syncwarp();
+#pragma unroll
+      for (int cc = 0; cc < KCS; ++cc) {
+        float v[32];
+        tmem_ld32(lane_base + (uint32_t)(buf * NR + h * CHI + cc * 32), v);
+        unsigned char* rb = a2base + cc * 32 * 128;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+          *reinterpret_cast<uint32_t*>(rb + jj * 128 + uoff[jj & 7]) = to_tf32(v[jj]);
+      }
+      tc_fence_before();
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&t1empty[buf]);
+        mbar_arrive(a2full);
+      }
+      if (!mbar_wait(t2full, i & 1, a.err)) { *abort_flag = 1; break; }
+      tc_fence_after();
+      __syncwarp();
+      float* C = d.C[e] + ROW_C(d, mt * 128 + row) + (h ? d.plane_c : 0);
+#pragma unroll
+      for (int cc = 0; cc < KCS; ++cc) {
+        float v[32];
+        tmem_ld32(lane_base + (uint32_t)(4 * CHI + h * CHI + cc * 32), v);
+        float* Cc = C + cc * 32 * CHI;  // columns n2 = cc * 32 + jj at stride CHI
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) Cc[jj * CHI] = v[jj];
+      }
+      tc_fence_before();
+      __syncwarp();
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                 : "memory");
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -563,6 +881,12 @@ cudaError_t tc_stream_prepare() {
     result = cudaFuncSetAttribute(tc_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kSmemBytes);
     if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(tc_chain_kernel<32>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemBytes);
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(tc_chain_kernel<64>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmemBytes);
+    if (result == cudaSuccess)
       result = cudaFuncSetAttribute(tc_close_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kCSmemBytes);
     if (result == cudaSuccess)
@@ -668,6 +992,104 @@ cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* par
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_tc_reduce(d, part, p.splits, st);
+}
+
+
+// The second product reads exactly what the first writes, with the first's
+// innermost row level as its contracted index: for every row (o, j) and
+// column n1 of the first, element (o, n1; k = j) of the second.  Checked
+// element by element; the result depends only on the two descriptors'
+// strides, so it is kept per distinct pair.
+bool chain_layouts_match(const GemmDesc& d1, const GemmDesc& d2) {
+  const int chi = d1.N;
+  const int64_t key[] = {d1.M,   d1.N,   d1.M2,   d1.M3,   d1.c_m,  d1.c_m2, d1.c_m3,
+                         d1.c_n, d2.M2,  d2.M3,   d2.a_m,  d2.a_m2, d2.a_m3, d2.a_k2};
+  constexpr int nk = (int)(sizeof(key) / sizeof(key[0]));
+  static std::mutex mu;
+  static std::vector<std::pair<std::vector<int64_t>, bool>> cache;
+  std::vector<int64_t> kv(key, key + nk);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& c : cache)
+      if (c.first == kv) return c.second;
+  }
+  bool ok = true;
+  for (int m1 = 0; m1 < d1.M && ok; ++m1) {
+    const int o = m1 / chi, j = m1 - o * chi;
+    for (int n1 = 0; n1 < chi; ++n1) {
+      const int64_t w = ROW_C(d1, m1) + (int64_t)n1 * d1.c_n;
+      const int64_t r = ROW_A(d2, o * chi + n1) + (int64_t)j * d2.a_k2;
+      if (w != r) { ok = false; break; }
+    }
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache.emplace_back(kv, ok);
+  return ok;
+}
+
+bool tc_chain_encode(const GemmDesc& d1, const GemmDesc& d2, const float* const* A,
+                     const float* const* B1, const float* const* A2, const float* const* B2,
+                     float* const* C1, int n_outer, void* host_maps, TcStreamPlan* p) {
+  const int chi = d1.N;
+  auto mode_ok = [&](const GemmDesc& d) {
+    return d.prec == TN_TF32 && d.b_pre && d.K1 == 1 && d.K2 == chi && d.N == chi && !d.conj_a &&
+           !d.accumulate && d.n_inner == 1 && d.M == d1.M;
+  };
+  if (!mode_ok(d1) || !mode_ok(d2) || d1.a_k2 != 1 || (chi != 32 && chi != 64) ||
+      d1.M % 128 != 0 || n_outer < 1 || d1.plane_c != d2.plane_a || d2.c_n != chi)
+    return false;
+  if (!chain_layouts_match(d1, d2)) return false;
+  for (int e = 0; e < n_outer; ++e)
+    if (A2[e] != C1[e] || (reinterpret_cast<uintptr_t>(B2[e]) & 15)) return false;
+  if (tc_stream_prepare() != cudaSuccess) return false;
+  // the A and Bt1 maps as for the streaming kernel, with chi-row Bt boxes
+  std::vector<unsigned char> tmp(tc_stream_map_bytes(n_outer) + 64);
+  unsigned char* t2 = (unsigned char*)(((uintptr_t)tmp.data() + 63) & ~uintptr_t(63));
+  TcStreamPlan sp;
+  if (!tc_stream_encode(d1, A, B1, n_outer, t2, &sp)) return false;
+  EncodeTiledFn enc = encode_fn();
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host_maps);
+  const CUtensorMap* src = reinterpret_cast<const CUtensorMap*>(t2);
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint64_t bd[2] = {(cuuint64_t)(2 * chi), (cuuint64_t)(2 * chi)};
+  const cuuint64_t bs[1] = {(cuuint64_t)(2 * chi * 4)};
+  const cuuint32_t bb[2] = {32, (cuuint32_t)chi};
+  for (int e = 0; e < n_outer; ++e) {
+    maps[e] = src[e];
+    if (enc(&maps[n_outer + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(B1[e]),
+            bd, bs, bb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    if (enc(&maps[2 * n_outer + e], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            const_cast<float*>(B2[e]), bd, bs, bb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  *p = sp;
+  p->kind = 2;
+  return true;
+}
+
+size_t tc_chain_map_bytes(int n_outer) { return (size_t)3 * n_outer * sizeof(CUtensorMap); }
+
+cudaError_t launch_tc_chain(const GemmDesc& d1, const GemmDesc& d2, const TcStreamPlan& p,
+                            int* err, cudaStream_t st) {
+  cudaError_t e = tc_stream_prepare();
+  if (e != cudaSuccess) return e;
+  FuseArgs a;
+  a.maps = reinterpret_cast<const CUtensorMap*>(p.maps);
+  a.n_outer = p.n_outer;
+  a.tiles_per_entry = d1.M / 128;
+  a.rank = p.rank;
+  a.lev0 = p.lev0;
+  a.lev1 = p.lev1;
+  a.err = err;
+  const int total = a.n_outer * a.tiles_per_entry;
+  const int grid = total < g_num_sms ? total : g_num_sms;
+  if (d1.N == 64) tc_chain_kernel<64><<<grid, kFThreads, kFSmemBytes, st>>>(d2, a);
+  else tc_chain_kernel<32><<<grid, kFThreads, kFSmemBytes, st>>>(d2, a);
+  return cudaGetLastError();
 }
 
 }  // namespace tnbp

@@ -104,8 +104,10 @@ def test_streaming_sweep_matches_oracle_127(tnlib, chi):
             s.set_message(e, src, m)
         s.bp_converge(tol=1e30, max_iters=1)
         st = s.stats()
-        # every degree-3 chain's two mode products: 6 streaming launches per sweep
-        assert (st["tma_launches"] >= 6) if kern == "auto" else (st["tma_launches"] == 0)
+        # each degree-3 chain's two mode products run as one fused TMA launch
+        # (3 per sweep); at chi = 64 the three closes are TMA launches too
+        want = 3 if chi == 32 else 6
+        assert (st["tma_launches"] >= want) if kern == "auto" else (st["tma_launches"] == 0)
         got[kern] = {k: s.get_message(k[1], k[0]) for k in msgs}
         s.close()
     o = OB.BPState(g, chi)
