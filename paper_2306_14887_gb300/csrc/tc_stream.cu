@@ -437,7 +437,9 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
 // second MMA takes with Bt2.  The second accumulator goes to global memory as
 // in the streaming kernel.  Each realified message [[Re, Im], [-Im, Re]] is
 // held as its three distinct chi x chi blocks (the (1,1) block equals (0,0)),
-// and every MMA has N = chi.
+// stacked per 32-wide K chunk as rows [(0,1); (0,0); (1,0)] (t, s): the
+// operand for input plane s = 1 is rows 0..2chi-1 ((0,1) over (1,1) = (0,0)),
+// for s = 0 rows chi..3chi-1 ((0,0) over (1,0)), so every MMA has N = 2 chi.
 //   warp 0 (one thread)  TMA: Bt1 / Bt2 blocks per site, the A ring (4 slots);
 //   warp 1 (one thread)  MMA: stage 1 of each tile; stage 2 of the previous
 //                        tile as soon as its operand is complete (polled
@@ -452,8 +454,8 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
 constexpr int kFThreads = 320;
 constexpr int kFEpi = 8;
 constexpr int kFSlots = 4;
-constexpr int kFBlkChunk = 64 * 128;          // [chi <= 64 rows][32 floats]
-constexpr int kFBBytes = 3 * 2 * kFBlkChunk;  // 3 blocks x chi/32 chunks
+constexpr int kFStack = 3 * 64 * 128;         // one K chunk: [3 chi <= 192 rows][32 floats]
+constexpr int kFBBytes = 2 * kFStack;         // chi / 32 <= 2 K chunks
 constexpr int kFA2Bytes = 4 * kChunk;         // 2 chi / 32 chunks of [128][32]
 constexpr int kFA2Off = 2 * kFBBytes;
 constexpr int kFRingOff = kFA2Off + kFA2Bytes;
@@ -468,8 +470,8 @@ struct FuseArgs {
   int* err;
 };
 
-// realified block (t, s) of a message -> stored block index
-__device__ __forceinline__ int rblock(int t, int s) { return t == s ? 0 : (t == 0 ? 1 : 2); }
+// row of the block stack where the N = 2 chi operand for input plane s starts
+__device__ __forceinline__ int stack_row(int s, int chi) { return s == 0 ? chi : 0; }
 
 template <int CHI>
 __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, FuseArgs a) {
@@ -542,12 +544,13 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
         if (e != cur) {
           if (cur >= 0 && !mbar_wait(bempty, (bl - 1) & 1, a.err)) { *abort_flag = 1; break; }
           mbar_expect_tx(bfull, bbytes);
+          // stack position b holds block (t, s) = (0,1), (0,0), (1,0)
 #pragma unroll
           for (int b = 0; b < 3; ++b) {
-            const int t = b == 2 ? 1 : 0, s = b == 1 ? 1 : 0;
+            const int t = b == 2 ? 1 : 0, s = b == 0 ? 1 : 0;
 #pragma unroll
             for (int kk = 0; kk < KCS; ++kk) {
-              const int off = (b * 2 + kk) * kFBlkChunk;
+              const int off = kk * kFStack + b * CHI * 128;
               tma_load_2d(smem_u32(sB1 + off), b1maps + e, s * CHI + kk * 32, t * CHI, bfull);
               tma_load_2d(smem_u32(sB2 + off), b2maps + e, s * CHI + kk * 32, t * CHI, bfull);
             }
@@ -586,24 +589,22 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(2, 128, CHI);
+      const uint32_t idesc = make_idesc(2, 128, NR);
       const uint32_t acc2 = tmem + (uint32_t)(4 * CHI);
       int pend = -1;  // local tile whose stage 2 is not issued yet
       // stage 2 of local tile pend; its operand is complete
       auto issue2 = [&]() {
         tc_fence_after();
 #pragma unroll
-        for (int t = 0; t < 2; ++t)
+        for (int c = 0; c < KC; ++c) {
+          const int s = c / KCS, kk = c - s * KCS;
+          const uint32_t a0 = smem_u32(sA2 + c * kChunk);
+          const uint32_t b0 = smem_u32(sB2 + kk * kFStack + stack_row(s, CHI) * 128);
 #pragma unroll
-          for (int c = 0; c < KC; ++c) {
-            const int s = c / KCS, kk = c - s * KCS;
-            const uint32_t a0 = smem_u32(sA2 + c * kChunk);
-            const uint32_t b0 = smem_u32(sB2 + (rblock(t, s) * 2 + kk) * kFBlkChunk);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              mma_issue(0, acc2 + (uint32_t)(t * CHI), sw128_desc(a0 + ks * 32),
-                        sw128_desc(b0 + ks * 32), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-          }
+          for (int ks = 0; ks < 4; ++ks)
+            mma_issue(0, acc2, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+                      (c > 0 || ks > 0) ? 1u : 0u);
+        }
         mma_commit(t2full);
         pend = -1;
       };
@@ -652,14 +653,11 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
           tc_fence_after();
           const int s = c / KCS, kk = c - s * KCS;
           const uint32_t a0 = smem_u32(sA + slot * kChunk);
+          const uint32_t b0 = smem_u32(sB1 + kk * kFStack + stack_row(s, CHI) * 128);
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const uint32_t b0 = smem_u32(sB1 + (rblock(t, s) * 2 + kk) * kFBlkChunk);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              mma_issue(0, acc1 + (uint32_t)(t * CHI), sw128_desc(a0 + ks * 32),
-                        sw128_desc(b0 + ks * 32), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-          }
+          for (int ks = 0; ks < 4; ++ks)
+            mma_issue(0, acc1, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+                      (c > 0 || ks > 0) ? 1u : 0u);
           mma_commit(&empty[slot]);
         }
         if (!ok) break;
