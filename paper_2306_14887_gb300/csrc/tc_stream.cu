@@ -224,9 +224,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
           tc_fence_after();
           const uint32_t a0 = smem_u32(sA + slot * kChunk);
           const uint32_t b0 = smem_u32(sB + c * a.nr * 128);
+          // descriptors of the chunk; a 32-byte K step adds 2 to the start field
+          const uint64_t da = sw128_desc(a0), db = sw128_desc(b0);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            mma_issue(0, d_tmem, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+            mma_issue(0, d_tmem, da + 2 * ks, db + 2 * ks, idesc,
                       (c > 0 || ks > 0) ? 1u : 0u);
           mma_commit(&empty[slot]);
         }
@@ -373,9 +375,11 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
         if (!mbar_wait(&full[slot], (i / kCStages) & 1, a.err)) { *abort_flag = 1; break; }
         tc_fence_after();
         const uint32_t a0 = smem_u32(smem + slot * kCStage);
+        // descriptors of the chunk; a 32-byte K step adds 2 to the start field
+        const uint64_t da = sw128_desc(a0), db = sw128_desc(a0 + kChunk);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
-          mma_issue(0, tmem, sw128_desc(a0 + ks * 32), sw128_desc(a0 + kChunk + ks * 32), idesc,
+          mma_issue(0, tmem, da + 2 * ks, db + 2 * ks, idesc,
                     (i > 0 || ks > 0) ? 1u : 0u);
         mma_commit(&empty[slot]);
       }
@@ -600,9 +604,11 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
           const int s = c / KCS, kk = c - s * KCS;
           const uint32_t a0 = smem_u32(sA2 + c * kChunk);
           const uint32_t b0 = smem_u32(sB2 + kk * kFStack + stack_row(s, CHI) * 128);
+          // descriptors of the chunk; a 32-byte K step adds 2 to the start field
+          const uint64_t da = sw128_desc(a0), db = sw128_desc(b0);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            mma_issue(0, acc2, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+            mma_issue(0, acc2, da + 2 * ks, db + 2 * ks, idesc,
                       (c > 0 || ks > 0) ? 1u : 0u);
         }
         mma_commit(t2full);
@@ -654,9 +660,11 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
           const int s = c / KCS, kk = c - s * KCS;
           const uint32_t a0 = smem_u32(sA + slot * kChunk);
           const uint32_t b0 = smem_u32(sB1 + kk * kFStack + stack_row(s, CHI) * 128);
+          // descriptors of the chunk; a 32-byte K step adds 2 to the start field
+          const uint64_t da = sw128_desc(a0), db = sw128_desc(b0);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            mma_issue(0, acc1, sw128_desc(a0 + ks * 32), sw128_desc(b0 + ks * 32), idesc,
+            mma_issue(0, acc1, da + 2 * ks, db + 2 * ks, idesc,
                       (c > 0 || ks > 0) ? 1u : 0u);
           mma_commit(&empty[slot]);
         }
