@@ -104,7 +104,8 @@ cudaError_t tc_stream_prepare();
 cudaError_t launch_tc_stream(const GemmDesc& d, const TcStreamPlan& p, int* err, cudaStream_t s);
 // Closes (tc_stream.cu): out[m][n] = sum_K A[m][K] op(B[n][K]), M = N = 64, both
 // operands K-contiguous, TF32; TMA-fed split-K into partials + the fixed-order
-// reduce.  part_floats bounds the partial buffer the caller provides.
+// reduce (a single split writes the output directly).  part_floats bounds the
+// partial buffer the caller provides.
 bool tc_close_encode(const GemmDesc& d, const float* const* A, const float* const* B, int n_outer,
                      size_t part_floats, void* host_maps, TcStreamPlan* p);
 cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* part, int* err,

@@ -459,7 +459,7 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
     if (L.sp.maps && L.sp.kind == 1) {
       TN_CUDA_TRY(launch_tc_close(L.d, L.sp, h->part, h->flags, h->stream));
       h->stats.tma_launches++;
-      nk = 2;
+      nk = L.sp.splits > 1 ? 2 : 1;  // the split-K reduce runs only for several splits
     } else if (L.sp.maps) {
       TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, h->stream));
       h->stats.tma_launches++;

@@ -42,6 +42,10 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cconjf(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+// (a, b, c, d) -> (a, c, b, d): two interleaved complex values <-> their real
+// pair and imaginary pair (the same permutation both ways)
+__device__ __forceinline__ float4 pair_swap(float4 v) { return make_float4(v.x, v.z, v.y, v.w); }
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -402,11 +406,17 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     // recomputed exactly at the start of each sweep, updated by each rotation,
     // which moves t |gamma| of weight from row p to row q
     // (alpha' = alpha - t|g|, beta' = beta + t|g|).
+    // Rows are held pair-split for the sweeps: each float4 carries the real
+    // parts of two consecutive complex values, then their imaginary parts, so
+    // that every complex dot product and rotation runs as paired FP32 FMAs
+    // (two lanes of arithmetic per instruction) without operand shuffles.
     float4* X4 = reinterpret_cast<float4*>(X);
     const int row4 = n / 2, nq = n / 32;
     const int sub = lane >> 4, gl = lane & 15;
     const int slot = warp * 2 + sub;
     const bool active = 2 * warp < half;  // warp-uniform: half is even
+    for (int idx = tid; idx < n * row4; idx += blockDim.x) X4[idx] = pair_swap(X4[idx]);
+    __syncthreads();
     for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
       ++sweeps;
       for (int j = warp; j < n; j += kWarps) {
@@ -445,18 +455,24 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
         for (int r = 0; r < B; ++r) {
           int rot = 0;
           if (active) {
-            const int q = s.order[g * 2 * B + B + (i + r) % B];
+            const int ir = i + r >= B ? i + r - B : i + r;  // (i + r) mod B, i, r < B
+            const int q = s.order[g * 2 * B + B + ir];
             float4 xq[4];
-            float gr = 0.f, gi = 0.f;
+            // gamma = sum conj(x_p) x_q: Re = sum pr qr + pi qi, Im = sum pr qi - pi qr
+            float2 ar = f2(0.f), ai = f2(0.f), aj = f2(0.f);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               if (u < nq) {
                 xq[u] = X4[q * row4 + gl + 16 * u];
-                // gamma = sum conj(x_p) x_q over the two complex values of the vector
-                gr += xs[u].x * xq[u].x + xs[u].y * xq[u].y + xs[u].z * xq[u].z + xs[u].w * xq[u].w;
-                gi += xs[u].x * xq[u].y - xs[u].y * xq[u].x + xs[u].z * xq[u].w - xs[u].w * xq[u].z;
+                const float2 pr = make_float2(xs[u].x, xs[u].y), pi = make_float2(xs[u].z, xs[u].w);
+                const float2 qr = make_float2(xq[u].x, xq[u].y), qi = make_float2(xq[u].z, xq[u].w);
+                ar = __ffma2_rn(pr, qr, ar);
+                ar = __ffma2_rn(pi, qi, ar);
+                ai = __ffma2_rn(pr, qi, ai);
+                aj = __ffma2_rn(pi, qr, aj);
               }
             }
+            float gr = ar.x + ar.y, gi = (ai.x + ai.y) - (aj.x + aj.y);
 #pragma unroll
             for (int o = 8; o > 0; o >>= 1) {
               gr += __shfl_xor_sync(0xffffffffu, gr, o);
@@ -491,17 +507,23 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
               float cs = rsqrtf(q2);
               cs = cs * (1.5f - 0.5f * q2 * cs * cs);
               const float sn = t * cs;
+              // pq = e^{-i phi} x_q; x_p <- cs x_p - sn pq, x_q <- sn x_p + cs pq,
+              // two complex values per paired operation
+              const float2 phr = f2(ph.x), phi = f2(ph.y), nphi = f2(-ph.y);
+              const float2 cs2 = f2(cs), sn2 = f2(sn), nsn2 = f2(-sn);
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 if (u < nq) {
-                  const float2 q0 = cmulf(ph, make_float2(xq[u].x, xq[u].y));
-                  const float2 q1 = cmulf(ph, make_float2(xq[u].z, xq[u].w));
-                  const float4 xp = xs[u];
-                  xs[u] = make_float4(cs * xp.x - sn * q0.x, cs * xp.y - sn * q0.y,
-                                      cs * xp.z - sn * q1.x, cs * xp.w - sn * q1.y);
-                  X4[q * row4 + gl + 16 * u] =
-                      make_float4(sn * xp.x + cs * q0.x, sn * xp.y + cs * q0.y,
-                                  sn * xp.z + cs * q1.x, sn * xp.w + cs * q1.y);
+                  const float2 pr = make_float2(xs[u].x, xs[u].y), pi = make_float2(xs[u].z, xs[u].w);
+                  const float2 qr = make_float2(xq[u].x, xq[u].y), qi = make_float2(xq[u].z, xq[u].w);
+                  const float2 pqr = __ffma2_rn(nphi, qi, __fmul2_rn(phr, qr));
+                  const float2 pqi = __ffma2_rn(phi, qr, __fmul2_rn(phr, qi));
+                  const float2 npr = __ffma2_rn(nsn2, pqr, __fmul2_rn(cs2, pr));
+                  const float2 npi = __ffma2_rn(nsn2, pqi, __fmul2_rn(cs2, pi));
+                  const float2 nqr = __ffma2_rn(sn2, pr, __fmul2_rn(cs2, pqr));
+                  const float2 nqi = __ffma2_rn(sn2, pi, __fmul2_rn(cs2, pqi));
+                  xs[u] = make_float4(npr.x, npr.y, npi.x, npi.y);
+                  X4[q * row4 + gl + 16 * u] = make_float4(nqr.x, nqr.y, nqi.x, nqi.y);
                 }
               }
               al = fmaxf(al - t * gm, 0.f);
@@ -521,6 +543,8 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
       }
       if (!any) break;
     }
+    for (int idx = tid; idx < n * row4; idx += blockDim.x) X4[idx] = pair_swap(X4[idx]);
+    __syncthreads();
   } else
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     ++sweeps;

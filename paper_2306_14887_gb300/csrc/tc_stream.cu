@@ -296,7 +296,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
 // through a 3-stage ring; K is split over CTAs, two CTAs per SM.  The
 // epilogue stages P in shared memory, combines C_re = P_rr - sa sb P_ii,
 // C_im = sb P_ri + sa P_ir and writes the CTA's partial; a second kernel sums
-// the partials in a fixed order.
+// the partials in a fixed order.  With one split the CTA writes the output
+// itself and no reduce runs.
 constexpr int kCThreads = 192;
 constexpr int kCStages = 3;
 constexpr int kCStage = 2 * kChunk;  // A 16 KB + B 16 KB
@@ -306,6 +307,7 @@ constexpr int kCSmemBytes = kCBarOff + 128 + 1024;
 struct CloseArgs {
   const CUtensorMap* maps;  // [2 * n_outer]: A maps, then B maps
   int n_outer, chunks, per_split, K2;
+  int direct;               // one split: the output is written here, no partials
   float* part;
   int* err;
 };
@@ -404,6 +406,8 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const float sa = d.conj_a ? -1.f : 1.f, sb = d.conj_b ? -1.f : 1.f;
     float* out = a.part + ((int64_t)split * a.n_outer + e) * 2 * 4096;
+    const int outer = e / d.n_inner, inner = e - outer * d.n_inner;
+    float* C = d.C[outer] + inner * d.c_in;
     for (int idx = tid - 64; idx < 4096; idx += 128) {
       const int m = idx >> 6, n = idx & 63;
       float cr = 0.f, ci = 0.f;
@@ -413,8 +417,14 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
         cr = prr - sa * sb * pii;
         ci = sb * pri + sa * pir;
       }
-      out[idx] = cr;
-      out[4096 + idx] = ci;
+      if (a.direct) {
+        float* pc = C + (int64_t)m * d.c_m + (int64_t)n * d.c_n;
+        pc[0] = cr;
+        pc[d.plane_c] = ci;
+      } else {
+        out[idx] = cr;
+        out[4096 + idx] = ci;
+      }
     }
   }
   tc_fence_before();
@@ -991,12 +1001,13 @@ cudaError_t launch_tc_close(const GemmDesc& d, const TcStreamPlan& p, float* par
   a.chunks = d.K1 * d.K2 / 32;
   a.per_split = (a.chunks + p.splits - 1) / p.splits;
   a.K2 = d.K2;
+  a.direct = p.splits == 1 ? 1 : 0;
   a.part = part;
   a.err = err;
   dim3 grid(p.splits, p.n_outer);
   tc_close_kernel<<<grid, kCThreads, kCSmemBytes, st>>>(d, a);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || a.direct) return e;
   return launch_tc_reduce(d, part, p.splits, st);
 }
 
