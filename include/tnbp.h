@@ -419,6 +419,26 @@ tn_status tn_server_get_stats(tn_server* s, tn_server_stats* out);
 tn_status tn_server_destroy(tn_server* s);
 
 /*
+ * tn_chi_extrapolate — linear extrapolation in 1/chi to infinite bond
+ * dimension (Main text, the n = 20 results and Fig. F2c, where a fit linear in
+ * 1/chi carries the BP-approximated TNS values to chi -> infinity).  For each
+ * of n_obs observables k, a least-squares fit of values[i * n_obs + k] =
+ * A_k + B_k / chi[i] over the n_chi bond dimensions:
+ *   chi       n_chi bond dimensions (host, caller-owned, each > 0, at least two
+ *             distinct);
+ *   values    n_chi x n_obs row-major (host), e.g. <Z_v> of a chi-ladder run
+ *             through the server;
+ *   intercept A_k, the chi -> infinity estimate (n_obs doubles, caller-owned);
+ *   slope     B_k (n_obs doubles, may be NULL);
+ *   rms       root-mean-square fit residual per observable (may be NULL).
+ * Host arithmetic only (FP64; no device call).  Errors: TN_EINVAL (NULL
+ * arguments, n_chi < 2, n_obs < 1, chi <= 0, all chi equal, non-finite
+ * values).
+ */
+tn_status tn_chi_extrapolate(const double* chi, const double* values, int32_t n_chi,
+                             int32_t n_obs, double* intercept, double* slope, double* rms);
+
+/*
  * tn_heavy_hex — the heavy-hex patch with `rows` rows (odd) of `cols` columns
  * (cols = 3 mod 4): row 0 has no last column, the last row no first column;
  * between rows r and r+1 a bridge qubit sits at columns = 0 mod 4 (r even) or

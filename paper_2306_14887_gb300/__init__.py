@@ -34,7 +34,7 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
            "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
-           "tn_load_state"]
+           "tn_load_state", "tn_chi_extrapolate"]
 
 
 class TNError(RuntimeError):
@@ -155,6 +155,7 @@ def lib():
         L.tn_server_wait.argtypes = [vp, C.c_uint64, C.c_double, dp, C.POINTER(tn_result)]
         L.tn_server_get_stats.argtypes = [vp, C.POINTER(tn_server_stats)]
         L.tn_server_destroy.argtypes = [vp]
+        L.tn_chi_extrapolate.argtypes = [dp, dp, i32, i32, dp, dp, dp]
         L.tn_last_error.restype = C.c_char_p
         L.tn_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -529,6 +530,47 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def chi_extrapolate(chis, values):
+    """Least-squares fit values[i, k] = A_k + B_k / chis[i] (tn_chi_extrapolate).
+
+    values: [len(chis), n_obs] (or [len(chis)]).  Returns (A, B, rms), A the
+    chi -> infinity estimate of each observable."""
+    x = np.ascontiguousarray(chis, dtype=np.float64).reshape(-1)
+    v = np.ascontiguousarray(values, dtype=np.float64).reshape(len(x), -1)
+    k = v.shape[1]
+    a, b, r = np.zeros(k), np.zeros(k), np.zeros(k)
+    P = C.POINTER(C.c_double)
+    _check(lib().tn_chi_extrapolate(x.ctypes.data_as(P), v.ctypes.data_as(P), len(x), k,
+                                    a.ctypes.data_as(P), b.ctypes.data_as(P),
+                                    r.ctypes.data_as(P)))
+    return a, b, r
+
+
+def theta_chi_sweep(server, n, edges, colours, thetas, chis, steps, prec="tf32", **cfg):
+    """A theta_h grid x chi ladder run as jobs of one server (they overlap on the
+    device as the server admits them), then extrapolated linearly in 1/chi.
+
+    Returns {"z": [n_theta, n_chi, n] <Z_v> after `steps` steps, "z_inf":
+    [n_theta, n] the intercepts, "slope", "rms", "steps_done": [n_theta, n_chi]}."""
+    tickets = {}
+    for i, th in enumerate(thetas):
+        for j, chi in enumerate(chis):
+            tickets[(i, j)] = server.submit(n, edges, colours, int(chi), float(th), int(steps),
+                                            prec=prec, **cfg)
+    z = np.zeros((len(thetas), len(chis), n))
+    done = np.zeros((len(thetas), len(chis)), dtype=np.int64)
+    for (i, j), t in tickets.items():
+        r = server.wait(t)
+        if r is None:
+            raise TNError(-7, "job %d did not finish in time" % t)
+        z[i, j], info = r
+        done[i, j] = info["steps_done"]
+    fits = [chi_extrapolate(chis, z[i]) for i in range(len(thetas))]
+    return {"z": z, "z_inf": np.stack([f[0] for f in fits]),
+            "slope": np.stack([f[1] for f in fits]), "rms": np.stack([f[2] for f in fits]),
+            "steps_done": done}
 
 
 def version():

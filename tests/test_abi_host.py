@@ -146,3 +146,31 @@ def test_server_rejects_bad_config_before_touching_a_device():
     cfg.max_slots = 0
     h = tn.C.c_void_p()
     assert tn.lib().tn_server_create(tn.C.byref(cfg), tn.C.byref(h)) == -1
+
+
+def test_chi_extrapolation_matches_least_squares():
+    """tn_chi_extrapolate: the least-squares line in 1/chi (host arithmetic)."""
+    r = np.random.default_rng(11)
+    chis = np.array([16.0, 32.0, 64.0, 128.0])
+    vals = r.standard_normal((4, 7))
+    a, b, rms = tn.chi_extrapolate(chis, vals)
+    X = np.stack([np.ones(4), 1.0 / chis], axis=1)
+    coef, *_ = np.linalg.lstsq(X, vals, rcond=None)
+    assert np.allclose(a, coef[0], atol=1e-12) and np.allclose(b, coef[1], atol=1e-12)
+    assert np.allclose(rms, np.sqrt(((X @ coef - vals) ** 2).mean(axis=0)), atol=1e-12)
+
+
+def test_chi_extrapolation_recovers_an_exact_line():
+    chis = np.array([8.0, 24.0, 500.0])
+    vals = np.stack([0.25 + 3.0 / chis, -1.0 + 0.0 / chis], axis=1)
+    a, b, rms = tn.chi_extrapolate(chis, vals)
+    assert np.allclose(a, [0.25, -1.0], atol=1e-13) and np.allclose(b, [3.0, 0.0], atol=1e-12)
+    assert np.all(rms < 1e-13)
+
+
+@pytest.mark.parametrize("chis,vals", [([16.0], [[1.0]]), ([16.0, 16.0], [[1.0], [2.0]]),
+                                       ([0.0, 16.0], [[1.0], [2.0]]),
+                                       ([8.0, 16.0], [[1.0], [np.nan]])])
+def test_chi_extrapolation_rejects_bad_input(chis, vals):
+    with pytest.raises(tn.TNError):
+        tn.chi_extrapolate(chis, vals)

@@ -83,3 +83,21 @@ def test_job_over_budget_is_refused(tnlib):
         with pytest.raises(tnlib.TNError) as ei:
             srv.submit(g.n, g.edges, g.colours, 16, 0.5, 1)
     assert ei.value.status == -2
+
+
+def test_theta_chi_sweep_extrapolates_to_the_oracle(tnlib):
+    """A theta grid x chi ladder as server jobs (FP32), extrapolated in 1/chi.
+    At theta = 0 every <Z_v> is 1; at theta = 0.6 and 3 steps every chi >= 8 is
+    exact for BP (bond dimension 2^3), so the slope vanishes and the intercept
+    is the oracle's value (two points: A = 2 y(16) - y(8), so 3 x 1e-6)."""
+    g = OG.falcon27_patch()
+    thetas, chis = [0.0, 0.6], [8, 16]
+    with tnlib.Server(slots=4) as srv:
+        out = tnlib.theta_chi_sweep(srv, g.n, g.edges, g.colours, thetas, chis, 3, prec="fp32")
+    assert (out["steps_done"] == 3).all()
+    assert np.abs(out["z"][0] - 1.0).max() < 1e-6 and np.abs(out["z_inf"][0] - 1.0).max() < 3e-6
+    want = OB.run(g, 8, 0.6, 3).all_z()
+    assert np.abs(out["z_inf"][1] - want).max() < 3e-6
+    assert np.abs(out["slope"][1]).max() < 1e-4
+    # the intercepts are the straight line through the two chi points
+    assert np.allclose(out["z_inf"], 2 * out["z"][:, 1] - out["z"][:, 0], atol=1e-12)
