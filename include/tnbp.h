@@ -340,6 +340,33 @@ tn_status tn_state_size(const tn_handle* h, size_t* bytes);
 tn_status tn_save_state(tn_handle* h, void* host, size_t bytes);
 tn_status tn_load_state(tn_handle* h, const void* host, size_t bytes);
 
+/*
+ * tn_vidal_gauge — the Vidal gauge (Gamma_v, lambda_e) of the state from its
+ * current BP messages (Methods, "The Vidal gauge" and "Belief propagation on
+ * a tensor network state": at the BP fixed point the messages define the
+ * gauge transformation to the Vidal form, exact on trees).  Per edge e =
+ * (u, w): P = sqrt(M_{u->w}), Q = sqrt(M_{w->u}) (Hermitian square roots of
+ * the messages u and w send across e), the SVD Q^T P = U diag(lambda) V^H
+ * (FP64 on the device), and the leg matrices Q conj(U) lambda^-1 (u's leg) and
+ * P V lambda^-1 (w's leg), which every site contracts into each of its legs
+ * (FP32) to give Gamma_v: T_v is Gamma_v with lambda_e^1/2 on every leg, and
+ * sum over the other indices of Gamma_v conj(Gamma_v) prod_{x != e} lambda_x^2
+ * is proportional to the identity on leg e at the fixed point.
+ *   lambda_out  n_edges x chi doubles (host, caller-owned): lambda_e in
+ *               decreasing order, unit 2-norm, zero past the messages'
+ *               support (below 1e-12 lambda_1).
+ * Call it on converged messages (tn_apply_floquet and tn_bp_converge end
+ * there).  Gamma is kept in the handle (one more state-sized buffer, allocated
+ * on the first call) until the next call; tn_get_gamma reads it.  The state
+ * and the messages are unchanged.  Errors: TN_EINVAL, TN_ENOMEM, TN_ECUDA,
+ * TN_ENUMERIC (a message with no support).
+ */
+tn_status tn_vidal_gauge(tn_handle* h, double* lambda_out);
+/* tn_get_gamma — Gamma_v of the last tn_vidal_gauge call, in the layout of
+ * tn_get_site (interleaved complex64, shape (2, chi, .., chi), 4 chi^d floats).
+ * Errors: TN_EINVAL (no tn_vidal_gauge yet, vertex out of range, buffer size). */
+tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats);
+
 /* tn_get_stats — counters of the last evolution call. */
 tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
 

@@ -34,7 +34,7 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
            "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
-           "tn_load_state", "tn_chi_extrapolate"]
+           "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma"]
 
 
 class TNError(RuntimeError):
@@ -156,6 +156,8 @@ def lib():
         L.tn_server_get_stats.argtypes = [vp, C.POINTER(tn_server_stats)]
         L.tn_server_destroy.argtypes = [vp]
         L.tn_chi_extrapolate.argtypes = [dp, dp, i32, i32, dp, dp, dp]
+        L.tn_vidal_gauge.argtypes = [vp, dp]
+        L.tn_get_gamma.argtypes = [vp, i32, C.POINTER(C.c_float), C.c_size_t]
         L.tn_last_error.restype = C.c_char_p
         L.tn_version.restype = C.c_char_p
         for name in EXPORTS:
@@ -424,6 +426,20 @@ class TNState:
                                  buf.size))
         z = buf[0::2] + 1j * buf[1::2]
         return z.reshape((2,) + (self.chi,) * d)
+
+    def vidal_gauge(self):
+        """lambda_e per edge ([n_edges, chi], decreasing, unit 2-norm) of the
+        Vidal gauge from the current messages; Gamma_v then via get_gamma."""
+        lam = np.zeros((len(self.edges), self.chi), dtype=np.float64)
+        _check(lib().tn_vidal_gauge(self._h, lam.ctypes.data_as(C.POINTER(C.c_double))))
+        return lam
+
+    def get_gamma(self, v):
+        d = self.degree(v)
+        buf = np.zeros(4 * self.chi ** d, dtype=np.float32)
+        _check(lib().tn_get_gamma(self._h, int(v), buf.ctypes.data_as(C.POINTER(C.c_float)),
+                                  buf.size))
+        return (buf[0::2] + 1j * buf[1::2]).reshape((2,) + (self.chi,) * d)
 
     def set_site(self, v, t):
         t = np.asarray(t, dtype=np.complex64).reshape(-1)

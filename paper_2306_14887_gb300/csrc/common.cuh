@@ -120,6 +120,15 @@ bool tc_chain_encode(const GemmDesc& d1, const GemmDesc& d2, const float* const*
 size_t tc_chain_map_bytes(int n_outer);
 cudaError_t launch_tc_chain(const GemmDesc& d1, const GemmDesc& d2, const TcStreamPlan& p,
                             int* err, cudaStream_t s);
+// Vidal gauge of every edge from the converged messages (solve.cu): per edge
+// e, dir[2e], dir[2e+1] the directed-message ids u->w and w->u; out the leg
+// matrices G_u, G_w (FP32 planar, [e][side][re|im][chi][chi]) and the
+// normalised bond weights lambda (FP64 [e][chi]).  work: vidal_work_doubles(chi)
+// per edge.
+size_t vidal_work_doubles(int chi);
+cudaError_t launch_vidal_edges(const float* msg, const int32_t* dir, int n_edges, int chi,
+                               double* work, float* gout, double* lam_out, int* flags,
+                               cudaStream_t s);
 // Kernel attributes set once, before any launch or stream capture.
 cudaError_t tc_prepare();
 cudaError_t normalise_prepare(int chi);

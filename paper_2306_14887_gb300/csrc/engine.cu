@@ -123,6 +123,8 @@ struct tn_handle {
 
   // backup for the extended-evolution expectation
   float *T_bak = nullptr, *msg_bak = nullptr;
+  // Vidal-gauge site tensors of the last tn_vidal_gauge call (same layout as T)
+  float* gamma = nullptr;
 
   tn_stats stats{};
   double* h_stats = nullptr;  // host copy of solve stats
@@ -1974,6 +1976,110 @@ tn_status tn_entanglement_entropy(tn_handle* h, int32_t e, double* out) {
     if (p > 0.0) s -= p * std::log2(p);
   }
   *out = s;
+  return TN_OK;
+}
+
+tn_status tn_vidal_gauge(tn_handle* h, double* lambda_out) {
+  if (!h || !lambda_out) { set_error("null argument"); return TN_EINVAL; }
+  const HostGraph& g = h->g;
+  const int E = (int)g.eu.size(), x = h->chi;
+  const int64_t c2 = (int64_t)x * x;
+  if (!h->gamma) {
+    h->gamma = (float*)dev_alloc(h, sizeof(float) * h->t_floats);
+    if (!h->gamma) { set_error("device allocation of the Vidal-gauge tensors failed"); return TN_ENOMEM; }
+  }
+  // per-edge scratch, leg matrices, bond weights, message ids and the pointer
+  // arena of the site contractions (one entry per site and leg: 2 E in all)
+  const size_t n_ptr = 3 * 2 * (size_t)E;
+  const size_t work_d = vidal_work_doubles(x) * (size_t)std::max(E, 1);
+  const size_t bytes = sizeof(double) * (work_d + (size_t)E * x) + sizeof(float) * 4 * c2 * E +
+                       sizeof(int32_t) * 2 * E + sizeof(void*) * n_ptr + 64;
+  unsigned char* buf = (unsigned char*)dev_alloc(h, bytes);
+  if (!buf) { set_error("device allocation for the Vidal gauge failed"); return TN_ENOMEM; }
+  double* work = (double*)buf;
+  double* lam = work + work_d;
+  float* gout = (float*)(lam + (size_t)E * x);
+  int32_t* ddir = (int32_t*)(gout + 4 * c2 * E);
+  void* arena = (void*)(((uintptr_t)(ddir + 2 * E) + 15) & ~uintptr_t(15));
+  auto fail_free = [&](tn_status code) { cudaStreamSynchronize(h->stream); dev_free(h, buf); return code; };
+  // Gamma_v = T_v with leg j contracted into the leg matrix of (v, legs[v][j]),
+  // leg by leg through the site-shaped intermediates
+  Plan P;
+  for (int d = 1; d <= 3; ++d) {
+    const std::vector<int>& sites = h->sites_by_deg[d];
+    if (sites.empty()) continue;
+    for (int j = 0; j < d; ++j) {
+      std::vector<std::array<const float*, 3>> ent;
+      for (int v : sites) {
+        const int e = g.legs[v][j];
+        const float* X = j == 0 ? site_ptr(h, h->T, v) : site_ptr(h, (j & 1) ? h->Y1 : h->Y2, v);
+        const float* Y = j == d - 1 ? h->gamma + h->t_off[v] : site_ptr(h, (j & 1) ? h->Y2 : h->Y1, v);
+        const float* G = gout + (int64_t)(2 * e + (g.eu[e] == v ? 0 : 1)) * 2 * c2;
+        ent.push_back({X, G, Y});
+      }
+      add_mode_product(P, d, j, x, TN_FP32, ent);
+    }
+  }
+  std::vector<int32_t> dir(2 * E);
+  for (int e = 0; e < E; ++e) {
+    dir[2 * e] = dir_id(g, g.eu[e], e);
+    dir[2 * e + 1] = dir_id(g, g.ew[e], e);
+  }
+  std::vector<const void*> host;
+  for (auto& L : P.L) {
+    for (auto q : L.A) host.push_back(q);
+    for (auto q : L.B) host.push_back(q);
+    for (auto q : L.C) host.push_back(q);
+  }
+  if (host.size() > n_ptr) return fail_free(TN_EINVAL);
+  if (E > 0 && (cudaMemcpyAsync(ddir, dir.data(), sizeof(int32_t) * 2 * E, cudaMemcpyHostToDevice,
+                                h->stream) != cudaSuccess ||
+                launch_vidal_edges(h->msg, ddir, E, x, work, gout, lam, h->flags, h->stream) !=
+                    cudaSuccess))
+    return fail_free(TN_ECUDA);
+  h->stats.kernel_launches += E > 0 ? 1 : 0;
+  if (!host.empty() && cudaMemcpyAsync(arena, host.data(), host.size() * sizeof(void*),
+                                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return fail_free(TN_ECUDA);
+  {
+    const void** base = (const void**)arena;
+    size_t pos = 0;
+    for (auto& L : P.L) {
+      L.d.A = (const float* const*)(base + pos); pos += L.A.size();
+      L.d.B = (const float* const*)(base + pos); pos += L.B.size();
+      L.d.C = (float* const*)(base + pos); pos += L.C.size();
+      // FP32 CUDA-core contractions whatever the handle's precision
+      if (launch_cgemm(L.d, h->stream) != cudaSuccess) return fail_free(TN_ECUDA);
+      h->stats.kernel_launches++;
+    }
+  }
+  for (int v : h->sites_by_deg[0])
+    if (cudaMemcpyAsync(h->gamma + h->t_off[v], site_ptr(h, h->T, v),
+                        sizeof(float) * 4 * h->t_len[v], cudaMemcpyDeviceToDevice,
+                        h->stream) != cudaSuccess)
+      return fail_free(TN_ECUDA);
+  if (E > 0 && cudaMemcpyAsync(lambda_out, lam, sizeof(double) * E * x, cudaMemcpyDeviceToHost,
+                               h->stream) != cudaSuccess)
+    return fail_free(TN_ECUDA);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_free(TN_ECUDA);
+  dev_free(h, buf);
+  return check_flags(h, "the Vidal gauge");
+}
+
+tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats) {
+  if (!h || !host_out) { set_error("null argument"); return TN_EINVAL; }
+  if (!h->gamma) { set_error("tn_vidal_gauge has not run on this handle"); return TN_EINVAL; }
+  if (v < 0 || v >= h->g.n) { set_error("vertex out of range"); return TN_EINVAL; }
+  const int64_t len = h->t_len[v];
+  if (n_floats != (size_t)(4 * len)) { set_error("site buffer must hold 4*chi^d floats"); return TN_EINVAL; }
+  std::vector<float> planar(4 * len);
+  TN_CUDA_TRY(cudaMemcpyAsync(planar.data(), h->gamma + h->t_off[v], sizeof(float) * 4 * len,
+                              cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int64_t i = 0; i < 2 * len; ++i) {
+    host_out[2 * i] = planar[i];
+    host_out[2 * i + 1] = planar[2 * len + i];
+  }
   return TN_OK;
 }
 

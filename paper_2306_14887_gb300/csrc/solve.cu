@@ -308,6 +308,144 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
   }
 }
 
+// Vidal gauge of one edge e = (u, w) from its two converged BP messages
+// (Methods, "The Vidal gauge": at the BP fixed point the messages define the
+// gauge transformation).  With P = sqrt(M_{u->w}), Q = sqrt(M_{w->u}) (the
+// Hermitian square roots of the messages u and w send across e) and the SVD
+// Q^T P = U diag(lambda) V^H, the bond matrices A = Q conj(U) lambda^-1/2 on
+// u's leg and B = P V lambda^-1/2 on w's leg satisfy A B^T = 1 on the
+// messages' support and turn both messages into diag(lambda).  The leg
+// matrices written out carry one more lambda^-1/2, so that contracting them
+// into the site tensors gives Gamma (T_v = Gamma_v with lambda^1/2 on every
+// leg): G_u = Q conj(U) / lambda, G_w = P V / lambda, FP32 planar
+// [side][re|im][i][k], and lambda / ||lambda||_2 (FP64, decreasing, zero past
+// the support).  The SVD is taken as the eigen-decomposition of Z^H Z, Z =
+// Q^T P, all in FP64; lambda below 1e-12 lambda_1 counts as zero.
+__global__ void __launch_bounds__(256) vidal_edge_kernel(const float* msg, const int32_t* dir,
+                                                         int chi, double* work, float* gout,
+                                                         double* lam_out, int* flags) {
+  __shared__ double sh[32];
+  __shared__ double rc[kMaxN / 2], rs[kMaxN / 2];
+  __shared__ cd rph[kMaxN / 2];
+  __shared__ double lam[kMaxN];
+  __shared__ int perm[kMaxN];
+  __shared__ double scal[2];
+  // the round-robin Jacobi pairs an even number of indices: odd chi is padded
+  // with one zero row and column (one more zero singular value, sorted last)
+  const int e = blockIdx.x, n = chi + (chi & 1);
+  const int64_t c2 = (int64_t)chi * chi, nn = (int64_t)n * n;
+  cd* base = reinterpret_cast<cd*>(work + (int64_t)e * 12 * nn);
+  cd* A = base;
+  cd* V = base + nn;
+  cd* Vs = base + 2 * nn;
+  cd* P = base + 3 * nn;
+  cd* Q = base + 4 * nn;
+  cd* Z = base + 5 * nn;
+  // 1. Hermitian square roots of the two messages: side 0 (u -> w) into P,
+  //    side 1 (w -> u) into Q.
+  for (int side = 0; side < 2; ++side) {
+    const float* m = msg + (int64_t)dir[2 * e + side] * 2 * c2;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int i = idx / n, j = idx - i * n;
+      cd a = {0.0, 0.0};
+      if (i < chi && j < chi) {
+        const int64_t o = (int64_t)i * chi + j, t = (int64_t)j * chi + i;
+        a = {0.5 * ((double)m[o] + (double)m[t]), 0.5 * ((double)m[c2 + o] - (double)m[c2 + t])};
+      }
+      A[idx] = a;
+    }
+    __syncthreads();
+    jacobi_eig(A, V, n, 40, sh, rc, rs, rph);
+    if (threadIdx.x == 0) {
+      double mx = 0.0;
+      for (int i = 0; i < n; ++i) mx = fmax(mx, A[i * n + i].x);
+      scal[0] = mx;
+    }
+    __syncthreads();
+    const double cut = 1e-14 * scal[0];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double d = A[i * n + i].x;
+      lam[i] = d > cut ? sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    cd* S = side == 0 ? P : Q;
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+      const int i = idx / n, j = idx - i * n;
+      cd acc = {0.0, 0.0};
+      for (int k = 0; k < n; ++k)
+        if (lam[k] > 0.0) acc = cadd(acc, cscale(cmul(V[i * n + k], cconj(V[j * n + k])), lam[k]));
+      S[idx] = acc;
+    }
+    __syncthreads();
+  }
+  // 2. Z = Q^T P; A = Z^H Z (Hermitised exactly) = V diag(lambda^2) V^H.
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    cd acc = {0.0, 0.0};
+    for (int k = 0; k < n; ++k) acc = cadd(acc, cmul(Q[k * n + i], P[k * n + j]));
+    Z[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    cd acc = {0.0, 0.0};
+    if (i <= j)
+      for (int k = 0; k < n; ++k) acc = cadd(acc, cmul(cconj(Z[k * n + i]), Z[k * n + j]));
+    A[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    if (i > j) A[idx] = cconj(A[j * n + i]);
+    else if (i == j) A[idx].y = 0.0;
+  }
+  __syncthreads();
+  jacobi_eig(A, V, n, 40, sh, rc, rs, rph);
+  sort_eig(A, V, Vs, n, lam, perm);
+  if (threadIdx.x == 0) {
+    const double l0 = lam[0] > 0.0 ? sqrt(lam[0]) : 0.0;
+    double nrm2 = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double l = lam[k] > 0.0 ? sqrt(lam[k]) : 0.0;
+      lam[k] = (l0 > 0.0 && l > 1e-12 * l0) ? l : 0.0;
+      nrm2 += lam[k] * lam[k];
+    }
+    scal[1] = sqrt(nrm2);
+    if (!(scal[1] > 0.0) || !isfinite(scal[1])) atomicOr(flags, 1);
+  }
+  __syncthreads();
+  // 3. U = Z V / lambda (into A); G_u = Q conj(U) / lambda, G_w = P V / lambda.
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    const int i = idx / n, k = idx - i * n;
+    cd acc = {0.0, 0.0};
+    if (lam[k] > 0.0) {
+      for (int j = 0; j < n; ++j) acc = cadd(acc, cmul(Z[i * n + j], Vs[j * n + k]));
+      acc = cscale(acc, 1.0 / lam[k]);
+    }
+    A[idx] = acc;
+  }
+  __syncthreads();
+  float* gu = gout + (int64_t)e * 4 * c2;
+  float* gw = gu + 2 * c2;
+  for (int idx = threadIdx.x; idx < c2; idx += blockDim.x) {
+    const int i = idx / chi, k = idx - i * chi;
+    cd au = {0.0, 0.0}, aw = {0.0, 0.0};
+    if (lam[k] > 0.0) {
+      for (int j = 0; j < n; ++j) {
+        au = cadd(au, cmul(Q[i * n + j], cconj(A[j * n + k])));
+        aw = cadd(aw, cmul(P[i * n + j], Vs[j * n + k]));
+      }
+      au = cscale(au, 1.0 / lam[k]);
+      aw = cscale(aw, 1.0 / lam[k]);
+    }
+    gu[idx] = (float)au.x; gu[c2 + idx] = (float)au.y;
+    gw[idx] = (float)aw.x; gw[c2 + idx] = (float)aw.y;
+  }
+  const double nrm = scal[1];
+  for (int k = threadIdx.x; k < chi; k += blockDim.x)
+    lam_out[(int64_t)e * chi + k] = nrm > 0.0 ? lam[k] / nrm : 0.0;
+}
+
 }  // namespace
 
 size_t solve_work_doubles(int chi) { return (size_t)12 * (2 * chi) * (2 * chi); }
@@ -316,6 +454,24 @@ cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s) {
   if (a.n_edges <= 0) return cudaSuccess;
   if (2 * a.chi > kMaxN) return cudaErrorInvalidValue;
   solve_kernel<<<a.n_edges, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tnbp
+
+namespace tnbp {
+
+size_t vidal_work_doubles(int chi) {
+  const size_t n = (size_t)(chi + (chi & 1));
+  return 12 * n * n;
+}
+
+cudaError_t launch_vidal_edges(const float* msg, const int32_t* dir, int n_edges, int chi,
+                               double* work, float* gout, double* lam_out, int* flags,
+                               cudaStream_t s) {
+  if (n_edges <= 0) return cudaSuccess;
+  if (chi + 1 > kMaxN) return cudaErrorInvalidValue;
+  vidal_edge_kernel<<<n_edges, 256, 0, s>>>(msg, dir, chi, work, gout, lam_out, flags);
   return cudaGetLastError();
 }
 

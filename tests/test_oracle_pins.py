@@ -301,3 +301,102 @@ def test_periodic_cell_cover_invariance():
     za, zb = a.all_z(), b.all_z()
     assert np.allclose(zb[:5], za, atol=1e-10)
     assert np.allclose(zb[5:], za, atol=1e-10)
+
+
+# ------------------------------------------------------------ Vidal gauge
+from oracle import vidal as V  # noqa: E402
+
+
+def _tree_side(g, e):
+    u, w = g.edges[e]
+    seen, stack = {u}, [u]
+    while stack:
+        v = stack.pop()
+        for f in g.legs[v]:
+            if f != e and g.other(f, v) not in seen:
+                seen.add(g.other(f, v))
+                stack.append(g.other(f, v))
+    return sorted(seen)
+
+
+def _schmidt(psi, n, side):
+    t = psi.reshape([2] * n)  # axis n-1-q holds qubit q
+    a = [n - 1 - q for q in side]
+    b = [ax for ax in range(n) if ax not in a]
+    return np.linalg.svd(np.transpose(t, a + b).reshape(2 ** len(side), -1), compute_uv=False)
+
+
+def _contract_state(g, tensors, bond=None):
+    """Full contraction of a small network into amplitudes psi[q_{n-1} .. q_0]
+    (the statevector's ordering); bond[e] (optional) is a diagonal inserted on
+    edge e."""
+    letters = iter("abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ")
+    phys = [next(letters) for _ in range(g.n)]
+    elab = [next(letters) for _ in range(len(g.edges))]
+    terms, ops = [], []
+    for v in range(g.n):
+        terms.append(phys[v] + "".join(elab[e] for e in g.legs[v]))
+        ops.append(tensors[v])
+    if bond is not None:
+        for e in range(len(g.edges)):
+            terms.append(elab[e])
+            ops.append(bond[e])
+    out = "".join(phys[q] for q in reversed(range(g.n)))
+    return np.einsum(",".join(terms) + "->" + out, *ops, optimize=True).reshape(-1)
+
+
+def test_vidal_canonical_on_tree_and_loopy_fixed_point():
+    """Methods, "The Vidal gauge": contracting Gamma_v with lambda_x^2 on all
+    legs but one and conj(Gamma_v) gives the identity on that leg; at a BP
+    fixed point this holds on loopy graphs too (in the BP sense)."""
+    for g, chi, steps in [(G.star3_tree(), 16, 3), (G.ring(12), 8, 5)]:
+        st = B.run(g, chi, 0.6, steps)
+        gam, lam = V.vidal_gauge(st)
+        worst = 0.0
+        for v in range(g.n):
+            ll = [lam[e] for e in g.legs[v]]
+            for j in range(len(ll)):
+                worst = max(worst, V.canonical_residual(gam[v], ll, j))
+        assert worst < 1e-8, (g.n, worst)
+
+
+def test_vidal_lambda_are_schmidt_values_on_a_tree():
+    """On a tree the Vidal bond weights are the state's Schmidt values across
+    the edge (brute force: SVD of the statevector across the cut)."""
+    g = G.star3_tree()
+    st = B.run(g, 16, 0.7, 3)
+    psi = S.evolve(g, 0.7, 3)
+    _, lam = V.vidal_gauge(st)
+    for e in range(len(g.edges)):
+        sv = _schmidt(psi, g.n, _tree_side(g, e))
+        sv = sv / np.linalg.norm(sv)
+        k = len(lam[e])
+        assert np.abs(lam[e] - sv[:k]).max() < 1e-10
+        assert np.abs(sv[k:]).max(initial=0.0) < 1e-10
+
+
+def test_vidal_form_reproduces_the_state():
+    """Gamma and lambda (one lambda per edge between the Gammas) contract to the
+    same state as the original tensors, up to one global factor."""
+    g = G.star3_tree()
+    st = B.run(g, 16, 0.9, 3)
+    gam, lam = V.vidal_gauge(st)
+    a = _contract_state(g, st.T)
+    b = _contract_state(g, gam, bond=lam)
+    c = np.vdot(b, a) / np.vdot(b, b)
+    assert np.abs(a - c * b).max() < 1e-10 * np.abs(a).max()
+
+
+def test_vidal_edge_gauge_undoes_to_identity():
+    """A B^T = 1 on the support and both messages become diag(lambda)."""
+    r = rng(7)
+    d = 6
+    x = r.standard_normal((d, d)) + 1j * r.standard_normal((d, d))
+    y = r.standard_normal((d, d)) + 1j * r.standard_normal((d, d))
+    m_uw, m_wu = x @ x.conj().T, y @ y.conj().T
+    g_u, g_w, s = V.edge_gauge(m_uw, m_wu)
+    a = g_u * np.sqrt(s)
+    b = g_w * np.sqrt(s)
+    assert np.abs(a @ b.T - np.eye(d)).max() < 1e-9
+    assert np.abs(a.T @ m_uw @ a.conj() - np.diag(s)).max() < 1e-9 * s[0]
+    assert np.abs(b.T @ m_wu @ b.conj() - np.diag(s)).max() < 1e-9 * s[0]
