@@ -367,6 +367,32 @@ tn_status tn_vidal_gauge(tn_handle* h, double* lambda_out);
  * Errors: TN_EINVAL (no tn_vidal_gauge yet, vertex out of range, buffer size). */
 tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats);
 
+/*
+ * tn_bp_error — the BP error estimate of edge e (Methods, "Estimating the
+ * error of BP for general tensor networks", Eq. BPErrorEstimate): the norm
+ * network of the state in the symmetric gauge (the Vidal gauge of
+ * tn_vidal_gauge with lambda^1/2 on every leg) is cut along e and contracted
+ * exactly to the chi^2 x chi^2 edge environment E (rows: the cut index on
+ * e's first endpoint, ket x bra; columns: on its second); BP takes E as rank
+ * one, and *error = 1 - sqrt(s_1^2 / sum_i s_i^2) over E's singular values s.
+ * Exact contraction is exponential in the loops' size: meant for small
+ * patches (a few heavy hexagons at small chi).  Host FP64 after the device
+ * gauge; each bond keeps only the support of its lambda.
+ *   sv_out       optional (may be NULL): the singular values of E in
+ *                decreasing order, up to sv_capacity of them;
+ *   n_sv         optional: their number (the squared support of lambda_e).
+ * Errors: TN_EINVAL (edge out of range, or an intermediate tensor above 2^26
+ * elements: the network is too large to contract exactly), TN_ENUMERIC, and
+ * those of tn_vidal_gauge.  Leaves the Vidal-gauge tensors of the handle set.
+ */
+tn_status tn_bp_error(tn_handle* h, int32_t e, double* error, double* sv_out,
+                      int32_t sv_capacity, int32_t* n_sv);
+/* tn_graph_info — the handle's vertex and edge counts and chi; edges_out
+ * (2 * capacity ints, may be NULL) receives the edges (u, w) in edge-id
+ * order.  Errors: TN_EINVAL (NULL counts, capacity below the edge count). */
+tn_status tn_graph_info(const tn_handle* h, int32_t* n_vertices, int32_t* n_edges, int32_t* chi,
+                        int32_t* edges_out, int32_t capacity);
+
 /* tn_get_stats — counters of the last evolution call. */
 tn_status tn_get_stats(const tn_handle* h, tn_stats* out);
 

@@ -34,7 +34,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
            "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
-           "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma"]
+           "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma",
+           "tn_bp_error", "tn_graph_info"]
 
 
 class TNError(RuntimeError):
@@ -157,6 +158,9 @@ def lib():
         L.tn_server_destroy.argtypes = [vp]
         L.tn_chi_extrapolate.argtypes = [dp, dp, i32, i32, dp, dp, dp]
         L.tn_vidal_gauge.argtypes = [vp, dp]
+        L.tn_bp_error.argtypes = [vp, i32, dp, dp, i32, C.POINTER(i32)]
+        L.tn_graph_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                    C.POINTER(i32), i32]
         L.tn_get_gamma.argtypes = [vp, i32, C.POINTER(C.c_float), C.c_size_t]
         L.tn_last_error.restype = C.c_char_p
         L.tn_version.restype = C.c_char_p
@@ -433,6 +437,17 @@ class TNState:
         lam = np.zeros((len(self.edges), self.chi), dtype=np.float64)
         _check(lib().tn_vidal_gauge(self._h, lam.ctypes.data_as(C.POINTER(C.c_double))))
         return lam
+
+    def bp_error(self, e):
+        """(1 - sqrt(index of separability), singular values of the edge
+        environment) of edge e in the symmetric gauge (tn_bp_error)."""
+        err = C.c_double()
+        cap = self.chi * self.chi
+        sv = np.zeros(cap, dtype=np.float64)
+        nsv = C.c_int32()
+        _check(lib().tn_bp_error(self._h, int(e), C.byref(err),
+                                 sv.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(nsv)))
+        return err.value, sv[:nsv.value]
 
     def get_gamma(self, v):
         d = self.degree(v)

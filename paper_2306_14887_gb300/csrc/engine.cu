@@ -2066,6 +2066,23 @@ tn_status tn_vidal_gauge(tn_handle* h, double* lambda_out) {
   return check_flags(h, "the Vidal gauge");
 }
 
+tn_status tn_graph_info(const tn_handle* h, int32_t* n_vertices, int32_t* n_edges, int32_t* chi,
+                        int32_t* edges_out, int32_t capacity) {
+  if (!h || !n_vertices || !n_edges || !chi) { set_error("null argument"); return TN_EINVAL; }
+  const int32_t m = (int32_t)h->g.eu.size();
+  *n_vertices = h->g.n;
+  *n_edges = m;
+  *chi = h->chi;
+  if (edges_out) {
+    if (capacity < m) { set_error("edge buffer too small"); return TN_EINVAL; }
+    for (int32_t e = 0; e < m; ++e) {
+      edges_out[2 * e] = h->g.eu[e];
+      edges_out[2 * e + 1] = h->g.ew[e];
+    }
+  }
+  return TN_OK;
+}
+
 tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats) {
   if (!h || !host_out) { set_error("null argument"); return TN_EINVAL; }
   if (!h->gamma) { set_error("tn_vidal_gauge has not run on this handle"); return TN_EINVAL; }

@@ -400,3 +400,42 @@ def test_vidal_edge_gauge_undoes_to_identity():
     assert np.abs(a @ b.T - np.eye(d)).max() < 1e-9
     assert np.abs(a.T @ m_uw @ a.conj() - np.diag(s)).max() < 1e-9 * s[0]
     assert np.abs(b.T @ m_wu @ b.conj() - np.diag(s)).max() < 1e-9 * s[0]
+
+
+# ------------------------------------------------------- BP error estimate
+from oracle import bperror as BE  # noqa: E402
+
+
+def test_bp_error_vanishes_on_a_tree():
+    """On a tree the cut norm network factorises: E = M_{u->w} (x) M_{w->u},
+    rank one, so the estimate is zero."""
+    g = G.star3_tree()
+    st = B.run(g, 8, 0.7, 3)
+    for e in range(len(g.edges)):
+        err, s = BE.bp_error(st, e)
+        assert err < 1e-12 and s[1] < 1e-10 * s[0]
+
+
+def test_bp_error_of_a_uniform_ring_is_the_transfer_matrix_closed_form():
+    """A ring of L equal site tensors, real and symmetric in their two legs:
+    the transfer matrix T[(l l'), (r r')] = sum_p t[p,l,r] t[p,l',r'] is real
+    symmetric, the symmetric gauge is an orthogonal change of the bond basis,
+    and the cut ring is T^L, so the singular values of E are |mu_k|^L for the
+    eigenvalues mu_k of T (the paper's exponential decay in the loop size)."""
+    r = rng(5)
+    chi = 3
+    t = r.standard_normal((2, chi, chi))
+    t = t + t.transpose(0, 2, 1)
+    tm = np.einsum("plr,pms->lmrs", t, t).reshape(chi * chi, chi * chi)
+    mu = np.linalg.eigvalsh(0.5 * (tm + tm.T))
+    for L in (4, 6, 8):
+        g = G.ring(L)
+        st = B.BPState(g, chi)
+        st.T = [t.astype(complex).copy() for _ in range(L)]
+        st.M = {k: np.eye(chi, dtype=complex) / np.sqrt(chi) for k in st.M}
+        st.bp_converge(tol=1e-13, max_iters=5000)
+        err, s = BE.bp_error(st, 0)
+        want = np.sort(np.abs(mu) ** L)[::-1]
+        want = want / want[0]
+        assert np.allclose(s / s[0], want, atol=1e-9)
+        assert abs(err - (1 - np.sqrt(1 / np.sum(want ** 2)))) < 1e-9
