@@ -125,6 +125,12 @@ struct tn_handle {
   float *T_bak = nullptr, *msg_bak = nullptr;
   // Vidal-gauge site tensors of the last tn_vidal_gauge call (same layout as T)
   float* gamma = nullptr;
+  // The captured sweep forks onto a second stream: sweep.L[sweep_split..] (the
+  // degree-2 chains and degree-1 closes, which share no scratch with the
+  // degree-3 chains) runs beside sweep.L[..sweep_split].
+  size_t sweep_split = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   tn_stats stats{};
   double* h_stats = nullptr;  // host copy of solve stats
@@ -432,8 +438,10 @@ bool use_tensor_cores(const tn_handle* h) {
   return h->cfg.prec != TN_FP32;
 }
 
-tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
-  for (size_t li = 0; li < P.L.size(); ++li) {
+tn_status run_plan(tn_handle* h, const Plan& P, int cls, size_t begin = 0,
+                   size_t end = (size_t)-1, bool on_side = false) {
+  const cudaStream_t stream = on_side ? h->side : h->stream;
+  for (size_t li = begin; li < P.L.size() && li < end; ++li) {
     const HostLaunch& L = P.L[li];
     if (L.skip) continue;
     const int pi = prof_begin(h, cls);
@@ -441,7 +449,7 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
     if (L.sp.maps && L.sp.kind == 2) {
       // two chain stages fused: the second stage's descriptor gives the output
       const GemmDesc& d2 = P.L[li + 1].d;
-      TN_CUDA_TRY(launch_tc_chain(L.d, d2, L.sp, h->flags, h->stream));
+      TN_CUDA_TRY(launch_tc_chain(L.d, d2, L.sp, h->flags, stream));
       h->stats.tma_launches++;
       if (pi >= 0) {
         double f1, b1, f2, b2;
@@ -459,16 +467,16 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
     const double macs = (double)L.d.n_outer * L.d.n_inner * L.d.M * L.d.N * L.d.K1 * L.d.K2;
     const bool tiny = macs < 262144.0;
     if (L.sp.maps && L.sp.kind == 1) {
-      TN_CUDA_TRY(launch_tc_close(L.d, L.sp, h->part, h->flags, h->stream));
+      TN_CUDA_TRY(launch_tc_close(L.d, L.sp, h->part, h->flags, stream));
       h->stats.tma_launches++;
       nk = L.sp.splits > 1 ? 2 : 1;  // the split-K reduce runs only for several splits
     } else if (L.sp.maps) {
-      TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, h->stream));
+      TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, stream));
       h->stats.tma_launches++;
     } else if (use_tensor_cores(h) && !tiny) {
-      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, h->stream, &nk));
+      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, stream, &nk));
     } else {
-      TN_CUDA_TRY(launch_cgemm(L.d, h->stream));
+      TN_CUDA_TRY(launch_cgemm(L.d, stream));
     }
     if (pi >= 0) {
       double f, b;
@@ -478,6 +486,27 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls) {
     h->stats.kernel_launches += nk;
   }
   return TN_OK;
+}
+
+// A launch may run on the side stream only if it does not use the shared
+// split-K partial buffer.
+bool side_safe(const tn_handle* h, const Plan& P, size_t begin) {
+  for (size_t li = begin; li < P.L.size(); ++li) {
+    const HostLaunch& L = P.L[li];
+    if (L.skip) continue;
+    if (L.sp.maps) {
+      if (L.sp.kind == 2 || (L.sp.kind == 1 && L.sp.splits > 1)) return false;
+      continue;
+    }
+    const double macs = (double)L.d.n_outer * L.d.n_inner * L.d.M * L.d.N * L.d.K1 * L.d.K2;
+    if (use_tensor_cores(h) && !(macs < 262144.0)) {
+      int q = 0, sp = 1;
+      size_t pf = 0;
+      tc_plan(L.d, &q, &sp, &pf);
+      if (sp > 1) return false;
+    }
+  }
+  return true;
 }
 
 const float* site_ptr(const tn_handle* h, const float* base, int v) { return base + h->t_off[v]; }
@@ -685,6 +714,7 @@ void build_sweep_plan(tn_handle* h) {
     for (int v : s3) outs.push_back((float*)msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][which])));
     deg3_chain(h, P, which, s3, false, outs);
   }
+  h->sweep_split = P.L.size();
   const std::vector<int>& s2 = h->sites_by_deg[2];
   for (int which = 0; which < 2; ++which) {
     std::vector<float*> outs;
@@ -1012,11 +1042,24 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
 
 // Enqueue one sweep: clear the status words, contract, normalise (residual and
 // flags accumulate in the status words), copy them to pinned host memory.
-tn_status enqueue_sweep(tn_handle* h) {
+tn_status enqueue_sweep(tn_handle* h, bool fork = false) {
   const int nmsg = 2 * (int)h->g.eu.size();
   TN_CUDA_TRY(cudaMemsetAsync(h->res_bits, 0, 2 * sizeof(unsigned long long), h->stream));
-  tn_status st = run_plan(h, h->sweep, P_BP);
-  if (st) return st;
+  tn_status st;
+  if (fork) {
+    // degree-2 and degree-1 launches on the side stream, beside the degree-3 chains
+    TN_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+    TN_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    st = run_plan(h, h->sweep, P_BP, h->sweep_split, (size_t)-1, true);
+    if (st) return st;
+    TN_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+    st = run_plan(h, h->sweep, P_BP, 0, h->sweep_split, false);
+    if (st) return st;
+    TN_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  } else {
+    st = run_plan(h, h->sweep, P_BP);
+    if (st) return st;
+  }
   const int pi = prof_begin(h, P_NORM);
   TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream,
                                h->mrt));
@@ -1036,9 +1079,20 @@ tn_status sweep_graph(tn_handle* h, bool* use) {
     cudaGraph_t graph = nullptr;
     const bool prof = h->prof_on;
     h->prof_on = false;
+    bool fork = h->sweep_split > 0 && h->sweep_split < h->sweep.L.size() &&
+                side_safe(h, h->sweep, h->sweep_split);
+    if (fork && !h->side) {
+      if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        fork = false;
+      }
+    }
+    fork = fork && h->side && h->ev_fork && h->ev_join;
     TN_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     const int64_t launches = h->stats.kernel_launches, tma = h->stats.tma_launches;
-    tn_status st = enqueue_sweep(h);
+    tn_status st = enqueue_sweep(h, fork);
     // the captured sweep's launch counts, charged once per graph launch
     h->sweep_kernels = h->stats.kernel_launches - launches;
     h->sweep_tma = h->stats.tma_launches - tma;
@@ -1454,6 +1508,9 @@ tn_status tn_destroy(tn_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->h_status) cudaFreeHost(h->h_status);
   dev_free_all(h);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
