@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances: the benchmark spec's bound for the plain FP32 path is |d<Z>| <= 1e-6
+Tolerances: the bound for the plain FP32 path is |d<Z>| <= 1e-6
 against the FP64 oracle; single kernels (one BP sweep, rho) are compared
 element by element at 2e-5 absolute on unit-norm messages, a few FP32 ulps
 times the contraction length.
