@@ -381,9 +381,11 @@ tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats
  *   sv_out       optional (may be NULL): the singular values of E in
  *                decreasing order, up to sv_capacity of them;
  *   n_sv         optional: their number (the squared support of lambda_e).
- * Errors: TN_EINVAL (edge out of range, or an intermediate tensor above 2^26
- * elements: the network is too large to contract exactly), TN_ENUMERIC, and
- * those of tn_vidal_gauge.  Leaves the Vidal-gauge tensors of the handle set.
+ * Errors: TN_EINVAL (edge out of range, an intermediate tensor above 2^26
+ * elements: the network is too large to contract exactly, or an edge
+ * environment above 1024 x 1024, i.e. a support above 32 on the cut edge),
+ * TN_ENUMERIC, and those of tn_vidal_gauge.  Leaves the Vidal-gauge tensors
+ * of the handle set.
  */
 tn_status tn_bp_error(tn_handle* h, int32_t e, double* error, double* sv_out,
                       int32_t sv_capacity, int32_t* n_sv);
