@@ -534,6 +534,19 @@ const char* tn_profile_class_name(int32_t cls);
 /* tn_last_error — message of the calling thread's last failed call ("" if none). */
 const char* tn_last_error(void);
 
+/*
+ * tn_selftest_bounded_wait — exercises the timeout path of the device-side
+ * waits (the paper has no counterpart; it is a check of this library's
+ * failure handling).  One thread waits, through the same bounded mbarrier wait
+ * the tensor-core kernels use, on a barrier nothing completes; after about one
+ * second the wait gives up and sets the timeout bit.  *flags_out receives the
+ * flag word: 2 (timeout) when the path works, 4 if the wait returned without
+ * giving up.  The call allocates 4 bytes of device memory and synchronises
+ * the stream (cuda_stream, may be NULL for the legacy default stream); the
+ * context stays usable afterwards.  Errors: TN_EINVAL, TN_ECUDA.
+ */
+tn_status tn_selftest_bounded_wait(void* cuda_stream, int32_t* flags_out);
+
 /* tn_version — library version string, static storage. */
 const char* tn_version(void);
 

@@ -35,7 +35,7 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
            "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma",
-           "tn_bp_error", "tn_graph_info"]
+           "tn_bp_error", "tn_graph_info", "tn_selftest_bounded_wait"]
 
 
 class TNError(RuntimeError):
@@ -158,6 +158,7 @@ def lib():
         L.tn_server_destroy.argtypes = [vp]
         L.tn_chi_extrapolate.argtypes = [dp, dp, i32, i32, dp, dp, dp]
         L.tn_vidal_gauge.argtypes = [vp, dp]
+        L.tn_selftest_bounded_wait.argtypes = [vp, C.POINTER(i32)]
         L.tn_bp_error.argtypes = [vp, i32, dp, dp, i32, C.POINTER(i32)]
         L.tn_graph_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                     C.POINTER(i32), i32]
@@ -602,6 +603,13 @@ def theta_chi_sweep(server, n, edges, colours, thetas, chis, steps, prec="tf32",
     return {"z": z, "z_inf": np.stack([f[0] for f in fits]),
             "slope": np.stack([f[1] for f in fits]), "rms": np.stack([f[2] for f in fits]),
             "steps_done": done}
+
+
+def selftest_bounded_wait(stream=None):
+    """Flag word of the bounded-wait self-test (2: the wait timed out as it must)."""
+    f = C.c_int32()
+    _check(lib().tn_selftest_bounded_wait(C.c_void_p(stream), C.byref(f)))
+    return f.value
 
 
 def version():

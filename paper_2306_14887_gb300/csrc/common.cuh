@@ -129,6 +129,9 @@ size_t vidal_work_doubles(int chi);
 cudaError_t launch_vidal_edges(const float* msg, const int32_t* dir, int n_edges, int chi,
                                double* work, float* gout, double* lam_out, int* flags,
                                cudaStream_t s);
+// Bounded-wait self-test (tc_stream.cu): a wait nothing completes; sets bit 1
+// of *err when it gives up (bit 2 if it returned without giving up).
+cudaError_t launch_wait_selftest(int* err, cudaStream_t s);
 // Kernel attributes set once, before any launch or stream capture.
 cudaError_t tc_prepare();
 cudaError_t normalise_prepare(int chi);

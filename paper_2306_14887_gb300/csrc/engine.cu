@@ -2123,6 +2123,22 @@ tn_status tn_vidal_gauge(tn_handle* h, double* lambda_out) {
   return check_flags(h, "the Vidal gauge");
 }
 
+tn_status tn_selftest_bounded_wait(void* cuda_stream, int32_t* flags_out) {
+  if (!flags_out) { set_error("null argument"); return TN_EINVAL; }
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  TN_CUDA_TRY(cudaMalloc(&d, sizeof(int)));
+  int f = 0;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_wait_selftest(d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&f, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  TN_CUDA_TRY(e);
+  *flags_out = f;
+  return TN_OK;
+}
+
 tn_status tn_graph_info(const tn_handle* h, int32_t* n_vertices, int32_t* n_edges, int32_t* chi,
                         int32_t* edges_out, int32_t capacity) {
   if (!h || !n_vertices || !n_edges || !chi) { set_error("null argument"); return TN_EINVAL; }

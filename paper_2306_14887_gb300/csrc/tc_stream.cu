@@ -755,6 +755,21 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
   }
 }
 
+// Self-test of the bounded device wait: one thread waits on an mbarrier that
+// nothing arrives at, through the same mbar_wait every tcgen05 kernel here
+// uses.  The wait must give up after its limit (about one second), set bit 1
+// of *err and return, leaving the context usable.
+__global__ void wait_selftest_kernel(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && mbar_wait(&bar, 0, err)) atomicOr(err, 4);  // 4: the wait did not give up
+  __syncthreads();
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -1106,6 +1121,12 @@ cudaError_t launch_tc_chain(const GemmDesc& d1, const GemmDesc& d2, const TcStre
   const int grid = total < g_num_sms ? total : g_num_sms;
   if (d1.N == 64) tc_chain_kernel<64><<<grid, kFThreads, kFSmemBytes, st>>>(d2, a);
   else tc_chain_kernel<32><<<grid, kFThreads, kFSmemBytes, st>>>(d2, a);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_wait_selftest(int* err, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(err);
   return cudaGetLastError();
 }
 
