@@ -104,12 +104,13 @@ typedef struct {
   double svd_cutoff;    /* singular values below svd_cutoff * sigma_1 are dropped;
                            <= 0 selects the precision's default */
   uint64_t seed;        /* reserved (the method draws no random numbers) */
-  int32_t solve;        /* truncation solve: TN_SOLVE_AUTO, TN_SOLVE_FP64 or TN_SOLVE_SHARED */
+  int32_t solve;        /* truncation solve: TN_SOLVE_AUTO, _REFINED, _FP64 or _SHARED */
   int32_t kernels;      /* contraction kernels: TN_KERNELS_AUTO or TN_KERNELS_TILE */
-  double solve_tol;     /* shared solve: Jacobi stops when every pair of rows of the bond
-                           matrix has |<x_p, x_q>| <= solve_tol ||x_p|| ||x_q||; <= 0 selects
-                           the precision's default (2e-6 for TN_FP32, 1e-4 for TN_TF32,
-                           1e-3 for TN_BF16: about the relative rounding of the Gram inputs) */
+  double solve_tol;     /* FP32 Jacobi of the shared and refined solves: it stops when every
+                           pair of rows of the bond matrix has |<x_p, x_q>| <= solve_tol
+                           ||x_p|| ||x_q||; <= 0 selects the default (refined: 2e-6, the
+                           FP32 floor; shared: 2e-6 for TN_FP32, 1e-4 for TN_TF32, 1e-3 for
+                           TN_BF16, about the relative rounding of the Gram inputs) */
 } tn_config;
 
 /* Contraction kernels of the tensor-core modes.
@@ -123,20 +124,29 @@ typedef struct {
 #define TN_KERNELS_AUTO 0
 #define TN_KERNELS_TILE 1
 
-/* Truncation solve variants.
- * TN_SOLVE_FP64: Hermitian Jacobi eigen-solves in FP64 on global-memory
- *   workspaces (all solve arithmetic FP64; slow on GB300, whose FP64 rate is
- *   about 1/64 of FP32).
- * TN_SOLVE_SHARED: FP64 pivoted Cholesky of the Gram blocks, then one-sided
- *   Jacobi of the 2chi x 2chi bond matrix in shared memory with FP32 rotations
- *   and the spectrum accumulated in FP64 (chi <= 64; larger chi fall back to
- *   TN_SOLVE_FP64).  Singular values to about 2e-6 relative; end to end about
- *   1e-5 in <Z> against the FP64 oracle.
- * TN_SOLVE_AUTO: TN_SOLVE_FP64 when prec is TN_FP32 (the plain path that must
- *   match the FP64 oracle to 1e-6 in <Z>), TN_SOLVE_SHARED otherwise. */
+/* Truncation solve variants (Methods, "The simple update procedure": the
+ * truncated SVD of the 2chi x 2chi bond matrix K = R_v R_w^T, taken as the
+ * eigen-decomposition of H = K K^H, from the Gram matrices of both sides).
+ * TN_SOLVE_REFINED: FP64 pivoted Cholesky of the v-side Gram blocks; an FP32
+ *   one-sided Jacobi of K in shared memory for a starting eigenbasis; one FP64
+ *   Newton step (the eigenvector refinement of Ogita and Aishima, 2018) of the
+ *   kept chi eigenvectors and eigenvalues of H = R_v conj(G_w) R_v^H; FP64 leg
+ *   matrices by triangular solves.  Every quantity the outputs are computed
+ *   from is FP64; the FP32 phase only chooses the basis the FP64 step starts
+ *   from (chi <= 64; larger chi fall back to TN_SOLVE_FP64).
+ * TN_SOLVE_FP64: Hermitian Jacobi eigen-solves of G_v and of H in FP64 on
+ *   global-memory workspaces (all arithmetic FP64; slow on GB300, whose FP64
+ *   rate is about 1/58 of its FP32 rate).  chi <= 256.
+ * TN_SOLVE_SHARED: everything in FP32 in shared memory except the spectrum's
+ *   norms (FP64): FP32 pivoted Cholesky of the Gram blocks, one-sided Jacobi of
+ *   K with FP32 rotations, FP32 triangular solves for the leg matrices
+ *   (chi <= 64; larger chi fall back to TN_SOLVE_FP64).  Singular values to
+ *   about 2e-6 relative; end to end about 1e-5 in <Z> against the FP64 oracle.
+ * TN_SOLVE_AUTO: TN_SOLVE_REFINED for chi <= 64, TN_SOLVE_FP64 above. */
 #define TN_SOLVE_AUTO 0
 #define TN_SOLVE_FP64 1
 #define TN_SOLVE_SHARED 2
+#define TN_SOLVE_REFINED 3
 
 /* Device allocator callbacks.  alloc returns device memory of at least `bytes`
  * bytes usable on `stream` (NULL on failure); free releases it. */
@@ -285,8 +295,9 @@ tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int
                               int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream);
 
 /* tn_truncation_solve_ex — tn_truncation_solve with the solve variant chosen:
- * TN_SOLVE_FP64 (what tn_truncation_solve runs; also for TN_SOLVE_AUTO) or
- * TN_SOLVE_SHARED (chi <= 64, TN_EUNSUPPORTED otherwise). */
+ * TN_SOLVE_FP64 (what tn_truncation_solve runs), TN_SOLVE_REFINED or
+ * TN_SOLVE_SHARED (both chi <= 64, TN_EUNSUPPORTED otherwise), or
+ * TN_SOLVE_AUTO (TN_SOLVE_REFINED for chi <= 64, TN_SOLVE_FP64 above). */
 tn_status tn_truncation_solve_ex(const float* gram, float* dmat, double* s_out, int32_t n_edges,
                                  int32_t chi, int32_t sign, double svd_cutoff, int32_t solve,
                                  void* cuda_stream);

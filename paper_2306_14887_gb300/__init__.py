@@ -21,7 +21,7 @@ STATUS = {0: "TN_OK", -1: "TN_EINVAL", -2: "TN_ENOMEM", -3: "TN_ENOTCONVERGED",
           -4: "TN_ENUMERIC", -5: "TN_ETIMEOUT", -6: "TN_ECUDA", -7: "TN_EAGAIN",
           -8: "TN_EUNSUPPORTED"}
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3, "tf32x3": 4}
-SOLVES = {"auto": 0, "fp64": 1, "shared": 2}
+SOLVES = {"auto": 0, "fp64": 1, "shared": 2, "refined": 3}
 KERNELS = {"auto": 0, "tile": 1}
 
 #: every symbol include/tnbp.h declares

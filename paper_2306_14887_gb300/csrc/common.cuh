@@ -194,11 +194,47 @@ struct SolveArgs {
   int max_sweeps;
   float orth_tol = 2e-6f;   // shared solve: pairs with |<x_p, x_q>| below
                             // orth_tol ||x_p|| ||x_q|| count as orthogonal
+  int basis = 0;            // shared solve in basis mode (the refined solve's FP32
+                            // phase): R_v from the FP64 Cholesky in work, output the
+                            // starting eigenbasis to work instead of the leg matrices
 };
+
+// Per-edge layout of the refined solve's workspace (offsets in doubles from the
+// edge's base work + edge * stride; complex values are pairs of doubles).
+struct RefineLayout {
+  int64_t L;      // [2][chi][chi] complex: FP64 Cholesky factors of the G_v blocks
+  int64_t U;      // [n][n] complex: starting basis, column m at U + 2 n m
+  int64_t U1;     // [chi][n] complex: refined kept columns
+  int64_t G;      // [n][n] complex: conj(G_w) in FP64
+  int64_t lam0;   // [n]: sigma^2 of the starting basis (decreasing)
+  int64_t lam1;   // [chi]: refined eigenvalues of the kept columns
+  int64_t misc;   // [4]: sum of all sigma^2 of the start, FP32 sweeps
+  int64_t ints;   // int32 [2 chi] perm, [2] rank, [1] active columns
+  int64_t stride;
+};
+__host__ __device__ inline RefineLayout refine_layout(int chi) {
+  const int64_t n = 2 * (int64_t)chi;
+  RefineLayout l;
+  l.L = 0;
+  l.U = l.L + 4 * (int64_t)chi * chi;
+  l.U1 = l.U + 2 * n * n;
+  l.G = l.U1 + 2 * n * chi;
+  l.lam0 = l.G + 2 * n * n;
+  l.lam1 = l.lam0 + n;
+  l.misc = l.lam1 + chi;
+  l.ints = l.misc + 4;
+  l.stride = 12 * n * n;  // solve_work_doubles(chi)
+  return l;
+}
 cudaError_t launch_solve(const SolveArgs& a, cudaStream_t s);
 size_t solve_work_doubles(int chi);
 // Shared-memory solve with FP32 rotations (solve32.cu), chi <= 64.
 bool solve32_supported(int chi);
 cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t s);
+// Refined solve (solve_refine.cu): FP64 Cholesky, FP32 starting basis, FP64
+// Newton refinement and FP64 leg matrices; chi <= 64.  work: solve_work_doubles
+// per edge.
+bool solve_refined_supported(int chi);
+cudaError_t launch_solve_refined(const SolveArgs& a, cudaStream_t s);
 
 }  // namespace tnbp

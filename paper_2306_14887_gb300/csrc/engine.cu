@@ -959,11 +959,12 @@ double default_svd_cut(const tn_handle* h) {
                                                                                        : 1e-4;
 }
 
-bool use_shared_solve(const tn_handle* h) {
-  const int sv = h->cfg.solve == TN_SOLVE_AUTO
-                     ? (h->cfg.prec == TN_FP32 ? TN_SOLVE_FP64 : TN_SOLVE_SHARED)
-                     : h->cfg.solve;
-  return sv == TN_SOLVE_SHARED && solve32_supported(h->chi);
+// The solve a handle runs: TN_SOLVE_REFINED, TN_SOLVE_SHARED or TN_SOLVE_FP64.
+int solve_kind(int solve, int chi) {
+  if (solve == TN_SOLVE_AUTO) solve = TN_SOLVE_REFINED;
+  if (solve == TN_SOLVE_REFINED && !solve_refined_supported(chi)) return TN_SOLVE_FP64;
+  if (solve == TN_SOLVE_SHARED && !solve32_supported(chi)) return TN_SOLVE_FP64;
+  return solve;
 }
 
 // Residual below which FP32-stored messages can no longer improve.
@@ -1000,7 +1001,13 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   a.s_out = h->spectra + h->spec_off[li] * h->chi;
   {
     const int pi = prof_begin(h, P_SOLVE);
-    if (use_shared_solve(h)) {
+    const int kind = solve_kind(h->cfg.solve, h->chi);
+    if (kind == TN_SOLVE_REFINED) {
+      a.max_sweeps = 20;
+      a.orth_tol = h->cfg.solve_tol > 0 ? (float)h->cfg.solve_tol : 2e-6f;
+      TN_CUDA_TRY(launch_solve_refined(a, h->stream));
+      h->stats.kernel_launches += 3;
+    } else if (kind == TN_SOLVE_SHARED) {
       a.max_sweeps = 20;
       a.orth_tol = (float)solve_tol(h);
       TN_CUDA_TRY(launch_solve32(a, h->stream));
@@ -1321,7 +1328,8 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   if (cfg->chi < 1 || cfg->chi > 256) { set_error("chi must be in 1..256"); return TN_EINVAL; }
   if (cfg->prec < TN_FP32 || cfg->prec > TN_TF32X3) { set_error("unknown precision"); return TN_EINVAL; }
 
-  if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64) {
+  if (cfg->solve != TN_SOLVE_AUTO && cfg->solve != TN_SOLVE_SHARED && cfg->solve != TN_SOLVE_FP64 &&
+      cfg->solve != TN_SOLVE_REFINED) {
     set_error("unknown truncation solve");
     return TN_EINVAL;
   }
@@ -2182,12 +2190,14 @@ tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int
 tn_status tn_truncation_solve_ex(const float* gram, float* dmat, double* s_out, int32_t n_edges,
                                  int32_t chi, int32_t sign, double svd_cutoff, int32_t solve,
                                  void* cuda_stream) {
-  if (solve != TN_SOLVE_AUTO && solve != TN_SOLVE_SHARED && solve != TN_SOLVE_FP64) {
+  if (solve != TN_SOLVE_AUTO && solve != TN_SOLVE_SHARED && solve != TN_SOLVE_FP64 &&
+      solve != TN_SOLVE_REFINED) {
     set_error("unknown truncation solve");
     return TN_EINVAL;
   }
-  if (solve == TN_SOLVE_SHARED && !solve32_supported(chi)) {
-    set_error("the shared-memory solve supports chi <= 64");
+  if ((solve == TN_SOLVE_SHARED && !solve32_supported(chi)) ||
+      (solve == TN_SOLVE_REFINED && !solve_refined_supported(chi))) {
+    set_error("the shared-memory and refined solves support chi <= 64");
     return TN_EUNSUPPORTED;
   }
   if (!gram || !dmat || !s_out) { set_error("null argument"); return TN_EINVAL; }
@@ -2219,9 +2229,13 @@ tn_status tn_truncation_solve_ex(const float* gram, float* dmat, double* s_out, 
   a.flags = (int*)flags;
   a.max_sweeps = 30;
   cudaError_t le;
-  if (solve == TN_SOLVE_SHARED) {
+  const int kind = solve_kind(solve, chi);
+  if (kind == TN_SOLVE_SHARED) {
     a.max_sweeps = 20;
     le = launch_solve32(a, st);
+  } else if (kind == TN_SOLVE_REFINED) {
+    a.max_sweeps = 20;
+    le = launch_solve_refined(a, st);
   } else {
     le = launch_solve(a, st);
   }

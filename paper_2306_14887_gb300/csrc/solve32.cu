@@ -206,6 +206,103 @@ __device__ Smem carve(unsigned char* base, int chi) {
   return s;
 }
 
+// Basis mode output (the refined solve's FP32 phase).  Column m of the
+// starting basis is row order[m] of the rotated K^T over its norm; lam0[m] =
+// sigma^2; the active count is the number of columns with sigma above 1e-6
+// sigma_1; the sum of sigma^2 and the sweep count go to misc.  The Jacobi
+// leaves pairs whose overlap is below its absolute floor unrotated, so
+// columns far below sigma_1 (the tail, sigma < 1e-3 sigma_1) can be far from
+// orthogonal; each active tail column is therefore orthogonalised against
+// every column before it and normalised (modified Gram-Schmidt in FP32, two
+// passes), which leaves the whole active basis orthonormal to about 1e-7.
+// Overwrites X and s.sig.
+__device__ __noinline__ void write_basis(const SolveArgs& a, const Smem& s, float2* X, int edge,
+                                         int chi, int sweeps) {
+  const int n = 2 * chi, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const RefineLayout lay = refine_layout(chi);
+  double* rbase = a.work + (int64_t)edge * lay.stride;
+  int* rints = reinterpret_cast<int*>(rbase + lay.ints);
+  const double s0 = s.sig[s.order[0]];
+  for (int m = tid; m < n; m += blockDim.x) {
+    const double sj = s.sig[s.order[m]];
+    rbase[lay.lam0 + m] = sj * sj;
+  }
+  if (tid == 0) {
+    int act = 0, head = 0;
+    double tot = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const double sj = s.sig[s.order[m]];
+      tot += sj * sj;
+      act += (sj > 0.0 && sj > 1e-6 * s0) ? 1 : 0;
+      head += (sj > 0.0 && sj >= 1e-3 * s0) ? 1 : 0;
+    }
+    rints[2 * chi + 2] = act;
+    s.counter[0] = act;
+    s.counter[1] = head;
+    rbase[lay.misc] = tot;
+    rbase[lay.misc + 1] = sweeps;
+    a.stats[4 * edge + 3] = sweeps;
+    if (!(s0 > 0.0) || !isfinite(tot)) atomicOr(a.flags, 1);
+  }
+  __syncthreads();
+  const int act = s.counter[0], head = s.counter[1];
+  // unit rows
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int j = idx / n;
+    const double sj = s.sig[j];
+    const float is = sj > 0.0 ? (float)(1.0 / sj) : 0.f;
+    X[idx] = make_float2(X[idx].x * is, X[idx].y * is);
+  }
+  __syncthreads();
+  if (head < act) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int k = 0; k < act; ++k) {
+        const int rk = s.order[k];
+        if (k >= head) {
+          // normalise tail row k (warp 0), every row before it being final
+          if (warp == 0) {
+            float acc = 0.f;
+            for (int c = lane; c < n; c += 32) {
+              const float2 v = X[rk * n + c];
+              acc += v.x * v.x + v.y * v.y;
+            }
+            acc = warp_sum(acc);
+            const float inv = acc > 0.f ? rsqrtf(acc) : 0.f;
+            for (int c = lane; c < n; c += 32) {
+              const float2 v = X[rk * n + c];
+              X[rk * n + c] = make_float2(v.x * inv, v.y * inv);
+            }
+          }
+          __syncthreads();
+        }
+        // x_m -= <u_k, x_m> u_k for the tail rows after k
+        for (int m = max(k + 1, head) + warp; m < act; m += kWarps) {
+          const int rm = s.order[m];
+          float gr = 0.f, gi = 0.f;
+          for (int c = lane; c < n; c += 32) {
+            const float2 u = X[rk * n + c], x = X[rm * n + c];
+            gr += u.x * x.x + u.y * x.y;
+            gi += u.x * x.y - u.y * x.x;
+          }
+          gr = warp_sum(gr);
+          gi = warp_sum(gi);
+          for (int c = lane; c < n; c += 32) {
+            const float2 u = X[rk * n + c], x = X[rm * n + c];
+            X[rm * n + c] = make_float2(x.x - (gr * u.x - gi * u.y), x.y - (gr * u.y + gi * u.x));
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  double2* U = reinterpret_cast<double2*>(rbase + lay.U);
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int m = idx / n, r = idx % n;
+    const float2 x = X[s.order[m] * n + r];
+    U[idx] = make_double2((double)x.x, (double)x.y);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int chi = a.chi, n = 2 * chi;
@@ -219,11 +316,27 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   const float sg = (float)a.sign;
 
   // 1. Gram matrices: G_v blocks conj(N_p^v) in Lv, G_w from conj(N_q^w) in X.
+  //    In basis mode Lv receives the FP64 Cholesky factors of the G_v blocks
+  //    (lower triangles, rounded) with their pivot orders and ranks instead.
   const int ldv = chi + 1;
-  for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
-    const int p = idx / (chi * chi), o = idx % (chi * chi);
-    s.Lv[p * chi * ldv + (o / chi) * ldv + o % chi] =
-        make_float2(gv[p * 2 * c2 + o], -gv[p * 2 * c2 + c2 + o]);
+  if (a.basis) {
+    const RefineLayout lay = refine_layout(chi);
+    const double* rbase = a.work + (int64_t)edge * lay.stride;
+    const int* rints = reinterpret_cast<const int*>(rbase + lay.ints);
+    const double2* L64 = reinterpret_cast<const double2*>(rbase + lay.L);
+    for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
+      const int p = idx / (chi * chi), o = idx % (chi * chi);
+      const double2 l = L64[idx];
+      s.Lv[p * chi * ldv + (o / chi) * ldv + o % chi] = make_float2((float)l.x, (float)l.y);
+    }
+    for (int i = tid; i < 2 * chi; i += blockDim.x) s.perm_v[i] = rints[i];
+    if (tid < 2) s.rank[tid] = rints[2 * chi + tid];
+  } else {
+    for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
+      const int p = idx / (chi * chi), o = idx % (chi * chi);
+      s.Lv[p * chi * ldv + (o / chi) * ldv + o % chi] =
+          make_float2(gv[p * 2 * c2 + o], -gv[p * 2 * c2 + c2 + o]);
+    }
   }
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx % n;
@@ -251,8 +364,9 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     const int half_t = kThreads / 2;
     const int h = tid >= half_t;
     const Group gh{h * half_t, half_t, 1 + h};
-    pivoted_cholesky32(s.Lv + h * chi * ldv, chi, ldv, s.perm_v + h * chi, ctol, &s.rank[h],
-                       s.red_i + h, s.red_v + h, s.dmax0 + h, colk + h * n, gh);
+    if (!a.basis)
+      pivoted_cholesky32(s.Lv + h * chi * ldv, chi, ldv, s.perm_v + h * chi, ctol, &s.rank[h],
+                         s.red_i + h, s.red_v + h, s.dmax0 + h, colk + h * n, gh);
     __syncthreads();
     const Group gall{0, kThreads, 0};
     pivoted_cholesky32(X, n, n, s.perm_w, ctol, &s.rank[2], s.red_i, s.red_v, s.dmax0 + 2, colk,
@@ -626,6 +740,10 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     s.order[rk] = i;
   }
   __syncthreads();
+  if (a.basis) {
+    write_basis(a, s, X, edge, chi, sweeps);
+    return;
+  }
   if (tid == 0) {
     double tot = 0.0, kept = 0.0;
     for (int i = 0; i < n; ++i) tot += s.sig[i] * s.sig[i];

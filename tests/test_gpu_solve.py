@@ -24,7 +24,7 @@ def tnlib():
     return tn
 
 
-def make_case(chi, rows, n_edges, seed):
+def make_case(chi, rows, n_edges, seed, decay=0.35):
     r = np.random.default_rng(seed)
     xs = []
     gram = np.zeros((n_edges, 2, 2, 2, chi, chi), dtype=np.float32)
@@ -32,7 +32,7 @@ def make_case(chi, rows, n_edges, seed):
         pair = []
         for side in range(2):
             x = (r.standard_normal((2, rows, chi)) + 1j * r.standard_normal((2, rows, chi)))
-            x *= np.exp(-0.35 * np.arange(chi))[None, None, :]   # decaying spectrum
+            x *= np.exp(-decay * np.arange(chi))[None, None, :]   # decaying spectrum
             pair.append(x)
             for p in range(2):
                 n_p = x[p].T @ x[p].conj()
@@ -64,11 +64,13 @@ def run_solve(tn, gram, chi, sign, n_edges, solve="fp64"):
     return d.cpu().numpy().reshape(gram.shape), s.cpu().numpy().reshape(n_edges, chi)
 
 
-@pytest.mark.parametrize("solve", ["fp64", "shared"])
+@pytest.mark.parametrize("solve", ["fp64", "shared", "refined"])
 @pytest.mark.parametrize("sign", [1, -1])
-@pytest.mark.parametrize("chi,rows", [(4, 6), (8, 12), (16, 20), (32, 40), (5, 3)])
+@pytest.mark.parametrize("chi,rows", [(4, 6), (8, 12), (16, 20), (32, 40), (5, 3), (64, 80)])
 def test_solve_matches_numpy_svd(tnlib, chi, rows, sign, solve):
     """Rows < chi makes the bond rank-deficient (padding regime)."""
+    if chi == 64 and solve == "fp64":
+        pytest.skip("the global-memory FP64 Jacobi takes seconds at chi = 64")
     n_edges = 5
     xs, gram = make_case(chi, rows, n_edges, seed=chi + 7 * rows + (sign > 0))
     dmat, s = run_solve(tnlib, gram, chi, sign, n_edges, solve)
@@ -100,3 +102,69 @@ def test_solve_rejects_bad_arguments(tnlib):
     with pytest.raises(tnlib.TNError) as ei:
         tnlib.truncation_solve(g.data_ptr(), g.data_ptr(), g.data_ptr(), 1, 300)
     assert ei.value.status == -1
+
+
+def gram_exact_spectrum(gram_k, chi, sign, cut=1e-6):
+    """The normalised kept spectrum of the problem the FP32 Gram inputs define,
+    in FP64 by NumPy: with the gate split on the projectors of v's physical
+    index, G_v = diag(conj N_0^v, conj N_1^v) and G_w[(k,e),(k',e')] =
+    sum_q conj(b_k(q)) b_k'(q) conj N_q^w[e,e'], b_k(q) = exp(s i pi/4 s_k s_q),
+    the squared singular values of the two-site matrix are the eigenvalues of
+    G_v^1/2 conj(G_w) G_v^1/2 (similar to G_v conj(G_w))."""
+    n = 2 * chi
+    nv = [(gram_k[0, p, 0] - 1j * gram_k[0, p, 1]).astype(complex) for p in range(2)]
+    nw = [(gram_k[1, q, 0] - 1j * gram_k[1, q, 1]).astype(complex) for q in range(2)]
+    gv = np.zeros((n, n), dtype=complex)
+    gv[:chi, :chi], gv[chi:, chi:] = nv[0], nv[1]
+    sk = np.array([1.0, -1.0])
+    gw = np.zeros((n, n), dtype=complex)
+    for k in range(2):
+        for k2 in range(2):
+            ph = [np.exp(-sign * 1j * np.pi / 4 * sk[k] * sk[q]) *
+                  np.exp(sign * 1j * np.pi / 4 * sk[k2] * sk[q]) for q in range(2)]
+            gw[k * chi:(k + 1) * chi, k2 * chi:(k2 + 1) * chi] = ph[0] * nw[0] + ph[1] * nw[1]
+    lam, w = np.linalg.eigh(0.5 * (gv + gv.conj().T))
+    root = (w * np.sqrt(np.clip(lam, 0.0, None))) @ w.conj().T
+    h = root @ gw.conj() @ root
+    ev = np.sort(np.linalg.eigvalsh(0.5 * (h + h.conj().T)))[::-1]
+    sv = np.sqrt(np.clip(ev, 0.0, None))[:chi]
+    sv = np.where(sv > cut * sv[0], sv, 0.0)
+    return sv / np.linalg.norm(sv)
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+@pytest.mark.parametrize("chi,rows", [(8, 12), (16, 20), (32, 40), (64, 80), (64, 4096)])
+def test_refined_spectrum_is_fp64_accurate(tnlib, chi, rows, sign):
+    """The refined solve's spectrum equals the exact FP64 spectrum of its own
+    (FP32-rounded) Gram inputs to 1e-11, well below the 2e-6 of the FP32
+    shared solve: every quantity it is computed from is FP64.  The decay keeps
+    every Gram eigenvalue above 1e-5 of the largest, far above the FP32
+    rounding of the inputs, so that the rounded Grams are positive definite
+    and their spectrum is defined to FP64 precision."""
+    n_edges = 6
+    _, gram = make_case(chi, rows, n_edges, seed=3 * chi + rows + (sign > 0),
+                        decay=5.0 / chi)
+    _, s = run_solve(tnlib, gram, chi, sign, n_edges, "refined")
+    _, s32 = run_solve(tnlib, gram, chi, sign, n_edges, "shared")
+    err = err32 = 0.0
+    for k in range(n_edges):
+        ref = gram_exact_spectrum(gram[k], chi, sign)
+        err = max(err, float(np.abs(s[k] - ref).max()))
+        err32 = max(err32, float(np.abs(s32[k] - ref).max()))
+    assert err < 1e-11, err
+    assert err32 > err   # the FP32 solve is the less accurate one
+
+
+def test_refined_legs_orthogonal_in_fp64_gram(tnlib):
+    """The left half X_v D_v of the refined solve is orthogonal with weights S:
+    sum_p D_v[p]^H conj(N_p^v) D_v[p] = diag(S), to the FP32 rounding of D."""
+    chi, rows, n_edges = 64, 80, 4
+    _, gram = make_case(chi, rows, n_edges, seed=99)
+    dmat, s = run_solve(tnlib, gram, chi, 1, n_edges, "refined")
+    for k in range(n_edges):
+        acc = np.zeros((chi, chi), dtype=complex)
+        for p in range(2):
+            d = dmat[k, 0, p, 0].astype(float) + 1j * dmat[k, 0, p, 1]
+            g = gram[k, 0, p, 0].astype(float) - 1j * gram[k, 0, p, 1]
+            acc += d.conj().T @ g @ d
+        assert np.abs(acc - np.diag(s[k])).max() < 2e-6
