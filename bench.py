@@ -5,8 +5,8 @@ heavy-hex (Eagle layout), chi = 64, on GB300.
                     [--chi 64] [--prec fp32] [--theta 0.8] [--presteps 7]
 
 One timed step = one application of U(theta_h) (RX on 127 qubits, 144 ZZ gates
-by BP-gauged simple update with the FP64 truncation solve, BP regauge to the
-tolerance).  The state is evolved `presteps` untimed steps first so that every
+by BP-gauged simple update with the refined FP64 truncation solve, BP regauge
+to the tolerance).  The state is evolved `presteps` untimed steps first so that every
 bond has reached chi (steps >= log2(chi) + 1), then W warm-up steps, then K
 timed steps bracketed by CUDA events on the library's stream.
 
@@ -40,7 +40,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 CSRC = os.path.join(ROOT, "paper_2306_14887_gb300", "csrc")
 
-# nominal figures (GB300): 152 SMs, 128 FP32 lanes per SM, 2070 MHz max clock
+# nominal figures (GB300), used only when a measurement is missing
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_TFLOPS = 1.25
 TF32_OVER_BF16 = 1.1 / 2.25
@@ -51,7 +51,8 @@ _CONTRACT = ("tc_stream.cu", "tc_gemm.cu", "tc_common.cuh", "kernels.cu")
 CLASS_SOURCE = {"bp_contract": _CONTRACT, "gate_env": _CONTRACT, "gate_rebuild": _CONTRACT,
                 "bp_normalise": ("kernels.cu",), "copyback": ("kernels.cu",),
                 "phys_gate": ("kernels.cu",), "rho": ("kernels.cu",),
-                "trunc_solve": ("solve32.cu", "solve.cu")}
+                "trunc_solve": ("solve32.cu", "solve.cu", "solve_refine.cu"),
+                "trunc_refine": ("solve_refine.cu",)}
 
 
 def parse():
@@ -64,7 +65,7 @@ def parse():
     p.add_argument("--prec", default="tf32")
     p.add_argument("--fp32-steps", type=int, default=3,
                    help="timed steps of the plain FP32 path measured beside the main line (0: skip)")
-    p.add_argument("--solve", default="auto", choices=["auto", "shared", "fp64"])
+    p.add_argument("--solve", default="auto", choices=["auto", "refined", "shared", "fp64"])
     p.add_argument("--kernels", default="auto", choices=["auto", "tile"])
     p.add_argument("--theta", type=float, default=None)
     p.add_argument("--presteps", type=int, default=None)
@@ -101,12 +102,29 @@ def max_over_ranks(ms, device):
     return float(t.item())
 
 
+SOLVE_NAMES = {
+    "refined": "refined FP64 (FP64 Cholesky, FP32 Jacobi start, FP64 Newton refinement and legs)",
+    "shared": "shared FP32 (FP32 Cholesky, Jacobi and legs)",
+    "fp64": "FP64 Jacobi eigen-solves",
+}
+
+
+def solve_kind(solve, chi):
+    """The truncation solve the library runs for --solve at this chi."""
+    if solve == "auto":
+        solve = "refined"
+    if solve in ("refined", "shared") and chi > 64:
+        return "fp64"
+    return solve
+
+
 def workload_config(args, world):
     """The workload both arms report (the reference arm times the oracle on it)."""
     chi = args.chi
     presteps = args.presteps if args.presteps is not None else int(np.log2(max(chi, 1))) + 1
     theta = theta_for(0, args)
-    return {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, solve={args.solve}, "
+    solve = SOLVE_NAMES[solve_kind(args.solve, chi)]
+    return {"workload": f"eagle127 heavy-hex, chi={chi}, prec={args.prec}, solve={solve}, "
                         f"theta_h={theta:.4f}, saturated after {presteps} steps",
             "qubits": 127, "edges": 144, "chi": chi,
             "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (
@@ -239,45 +257,85 @@ def bp_sweep_flops(chi, n_by_deg):
     return 8.0 * (16 * chi ** 4 * n_by_deg[3] + 8 * chi ** 3 * n_by_deg[2] + 2 * chi ** 2 * n_by_deg[1])
 
 
-def roofline(prof, prec, chi, sweeps, n_by_deg, shared_solve):
+def measure_peaks():
+    """TF32, FP32 (no TF32) and FP64 dense matmul rates of this GPU, measured the
+    way the BF16 figure of the peaks file was: torch.matmul on square matrices,
+    best of 5 after warm-up, CUDA events (TFLOP/s)."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, n, tf32 in (("tf32", torch.float32, 8192, True),
+                              ("fp32", torch.float32, 4096, False),
+                              ("fp64", torch.float64, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(5):
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        out[name + "_tflops"] = round(2.0 * n ** 3 / best / 1e12, 2)
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = "torch.matmul n^3 (tf32 8192, fp32 4096 without TF32, fp64 4096), best of 5"
+    return out
+
+
+def roofline(prof, prec, chi, sweeps, n_by_deg, solve, mp):
+    """The roofline of the dominant profile class of the timed region."""
     cls = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[cls]
     n = max(1, p["launches"])
     ms_per = p["ms"] / n
     pk = peaks()
+    bf16_sus = pk.get("bf16_tflops_sustained", 1715.0)
+    sus_ratio = bf16_sus / pk.get("bf16_tflops", bf16_sus)
     if cls == "bp_contract":
         # algorithmic work of the sweeps, not the executed (padded, re-ordered) work
         p = dict(p)
         p["flops"] = bp_sweep_flops(chi, n_by_deg) * sweeps
-    if cls == "trunc_solve":
-        # nominal 40 (2 chi)^3 flops per gate edge (the library's own count)
+    if cls == "trunc_refine":
+        # FP64 Newton step and leg matrices (the library's algorithmic count)
         bound, unit = "alu", "TFLOP/s"
-        peak = FP32_SIMT_TFLOPS if shared_solve else FP64_TFLOPS
+        peak = mp.get("fp64_tflops", FP64_TFLOPS)
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
-        note = ("FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz" if shared_solve
-                else "FP64 ALU, nominal 1.25 TFLOP/s")
+        note = "FP64: measured torch.matmul float64"
+    elif cls == "trunc_solve":
+        bound, unit = "alu", "TFLOP/s"
+        if solve == "fp64":
+            peak, note = mp.get("fp64_tflops", FP64_TFLOPS), "FP64: measured torch.matmul float64"
+        else:
+            peak, note = mp.get("fp32_tflops", FP32_SIMT_TFLOPS), "FP32: measured torch.matmul without TF32"
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
     elif cls in ("bp_contract", "gate_env", "gate_rebuild"):
         if prec == "fp32":
-            bound, unit, peak = "alu", "TFLOP/s", FP32_SIMT_TFLOPS
-            note = "FP32 CUDA cores: 152 SMs x 128 lanes x 2 x 2.07 GHz"
-        elif prec == "bf16":
+            bound, unit = "alu", "TFLOP/s"
+            peak, note = mp.get("fp32_tflops", FP32_SIMT_TFLOPS), "FP32: measured torch.matmul without TF32"
+        elif prec in ("bf16", "bf16x3"):
             bound, unit = "tensor", "TFLOP/s"
-            peak = pk.get("bf16_tflops_sustained", 1715.0)
-            note = "bf16 sustained"
+            peak, note = bf16_sus, "bf16 sustained (peaks file)"
         else:
             bound, unit = "tensor", "TFLOP/s"
-            peak = pk.get("bf16_tflops_sustained", 1715.0) * TF32_OVER_BF16
-            note = "tf32 = measured bf16 sustained x nominal tf32/bf16 ratio (1.1/2.25)"
+            peak = mp.get("tf32_tflops", pk.get("bf16_tflops", 1945.0) * TF32_OVER_BF16) * sus_ratio
+            note = ("tf32: measured torch.matmul TF32 burst x the peaks file's bf16 "
+                    "sustained/burst ratio (%.3f)" % sus_ratio)
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
     else:
         bound, unit, peak = "hbm", "GB/s", pk.get("hbm_gbs", 6792.1)
         achieved = p["bytes"] / (p["ms"] * 1e-3) / 1e9
-        note = "measured HBM copy"
+        note = "measured HBM copy (peaks file)"
     tr = traffic_for(cls)
     return {"bound": bound, "kernel": cls, "achieved": round(achieved, 3), "peak": round(peak, 3),
             "unit": unit, "frac": round(achieved / peak, 4),
             "traffic": tr, "launches": p["launches"], "ms_per_launch": round(ms_per, 4),
-            "share_of_timed": None, "peak_source": note + (" (of measured)" if bound in ("hbm", "tensor") else " (nominal)")}
+            "share_of_timed": None, "peak_source": note + " (of measured)"}
 
 
 # ------------------------------------------------------------ CPU oracle leg
@@ -303,6 +361,24 @@ def oracle_step_estimate(chi, bp_iters, n_gate_sample=6, seed=3):
     t_gate = (time.perf_counter() - t0) / len(pick)
     per_step = t_gate * len(g.edges) + bp_iters * t_sweep
     return per_step, {"t_sweep_s": t_sweep, "t_gate_s": t_gate, "gates_sampled": len(pick)}
+
+
+def oracle_single_thread(chi, bp_iters, n_gate_sample=2):
+    """The same bounded oracle sample in a fresh process with every BLAS and
+    OpenMP pool at one thread; returns (seconds per Floquet step, detail) or
+    None if the child fails."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = ("import json, bench; sec, det = bench.oracle_step_estimate(%d, %r, n_gate_sample=%d); "
+            "print(json.dumps([sec, det]))" % (chi, float(bp_iters), n_gate_sample))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                           text=True, timeout=600)
+        sec, det = json.loads(r.stdout.strip().splitlines()[-1])
+        return sec, det
+    except Exception:
+        return None
 
 
 def blas_threads():
@@ -331,6 +407,7 @@ def run_ours(args, rank, world, local):
     presteps = args.presteps if args.presteps is not None else int(np.log2(max(chi, 1))) + 1
     theta = theta_for(rank, args)
     n, edges, cols = eagle()
+    mp = measure_peaks()
     stream = torch.cuda.Stream()
     s = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream, solve=args.solve,
                      kernels=args.kernels)
@@ -394,17 +471,17 @@ def run_ours(args, rank, world, local):
                        "tn_apply_floquet (theta, 8 bytes, passed by value) and tn_expect_z_all "
                        "into host memory"}
     nbd = {d: int(sum(1 for v in range(n) if int(np.sum(edges == v)) == d)) for d in (1, 2, 3)}
-    shared_solve = args.solve == "shared" or (args.solve == "auto" and args.prec != "fp32")
-    rl = roofline(prof, args.prec, chi, bp_iters, nbd, shared_solve)
+    rl = roofline(prof, args.prec, chi, bp_iters, nbd, solve_kind(args.solve, chi), mp)
     rl["share_of_timed"] = round(prof[rl["kernel"]]["ms"] / ms, 4)
     serving = None
     if args.serve_jobs > 0 and rank == 0:
         serving = serve_leg(tn, args)
     fp32_line = None
     if args.fp32_steps > 0 and args.prec != "fp32":
-        s3 = tn.TNState(n, edges, cols, chi=chi, prec="fp32", stream=stream)
+        s3 = tn.TNState(n, edges, cols, chi=chi, prec="fp32", stream=stream, solve=args.solve)
         s3.apply_floquet(theta, presteps + 1)
         stream.synchronize()
+        s3.profile_enable(True)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -413,12 +490,17 @@ def run_ours(args, rank, world, local):
         f1.record(stream)
         stream.synchronize()
         fms = f0.elapsed_time(f1)
+        fprof = s3.profile()
+        s3.profile_enable(False)
         zf = s3.expect_z_all()
         s3.close()
         fp32_line = {"value": round(args.fp32_steps / (fms * 1e-3), 4), "unit": UNIT,
                      "steps": args.fp32_steps, "ms_per_step": round(fms / args.fp32_steps, 3),
-                     "note": "plain FP32 path (CUDA-core contractions, FP64 truncation solve), "
-                             "same workload and theta",
+                     "kernel_ms": {k: round(v["ms"], 3) for k, v in fprof.items()},
+                     "note": "plain FP32 path: CUDA-core FP32 contractions with the same "
+                             "truncation solve (%s), same workload and theta, so that "
+                             "mixed_over_fp32 compares the contraction precision alone"
+                             % SOLVE_NAMES[solve_kind(args.solve, chi)],
                      "mixed_over_fp32": None}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -432,6 +514,7 @@ def run_ours(args, rank, world, local):
         "bp_sweeps_per_step": round(bp_iters / args.steps, 2),
         "discarded_weight_max": disc,
         "roofline": rl,
+        "peaks_measured": mp,
         "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
         "clocks": clocks,
         "e2e": e2e,
@@ -444,13 +527,21 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sec, det = oracle_step_estimate(chi, bp_iters / args.steps)
         out["cpu_baseline"] = {"value": round(1.0 / sec, 6), "unit": UNIT, "cores": blas_threads(),
-                               "kind": "oracle",
+                               "kind": "oracle", "estimate": True,
                                "sample": "FP64 NumPy oracle on the 127-qubit chi=%d workload: one BP "
                                          "sweep and %d simple-update gates on a random full-chi "
-                                         "state, scaled to 144 gates + %.1f sweeps per step "
-                                         "(sweep %.2f s, gate %.2f s)" % (
+                                         "state timed, the step estimated as 144 gates + %.1f "
+                                         "sweeps (the GPU path's measured count) (sweep %.2f s, "
+                                         "gate %.2f s)" % (
                                              chi, det["gates_sampled"], bp_iters / args.steps,
                                              det["t_sweep_s"], det["t_gate_s"])}
+        one = oracle_single_thread(chi, bp_iters / args.steps)
+        if one is not None:
+            sec1, det1 = one
+            out["cpu_baseline"]["single_thread"] = {
+                "value": round(1.0 / sec1, 6), "unit": UNIT, "cores": 1, "estimate": True,
+                "sample": "the same sample with every BLAS/OpenMP pool at one thread (sweep %.2f s, "
+                          "gate %.2f s)" % (det1["t_sweep_s"], det1["t_gate_s"])}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -460,28 +551,38 @@ def run_ours(args, rank, world, local):
 
 # ---------------------------------------------------------------- reference
 def run_reference(args, rank, world):
+    """The FP64 oracle on bounded samples of the workload: each sample times one
+    synchronous BP sweep and two simple-update gates on a random full-chi
+    127-qubit state; a Floquet step is estimated as 144 gates + 16 sweeps (the
+    GPU path's measured count at this workload).  The line is labelled an
+    estimate, and `steps` counts the Floquet steps of work actually timed (the
+    samples' total time over the per-step estimate), so that steps x
+    ms_per_step is the timed work."""
     if rank != 0:
         return
     chi = args.chi
-    # sweeps per step used to scale the sample: the GPU arm's measured count at
-    # this workload (16.3 at chi = 64, TF32); the FP64 oracle would need more
     bp = 16.0
-    times = []
+    times, sample_s = [], 0.0
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         sec, det = oracle_step_estimate(chi, bp, n_gate_sample=2, seed=100 + i)
         if i >= args.warmup:
             times.append(sec)
+            sample_s += time.perf_counter() - t0
     per = float(np.mean(times))
     val = 1.0 / per
     out = {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": UNIT,
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "n_gpus": world, "steps": round(sample_s / per, 4), "warmup": args.warmup,
            "ms_per_step": round(per * 1e3, 2), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": workload_config(args, world),
+           "estimate": True, "samples": args.steps,
            "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": blas_threads(),
-                            "kind": "oracle",
-                            "sample": "each step: one BP sweep + 2 simple-update gates on a random "
-                                      "full-chi 127-qubit state, scaled to 144 gates + %.0f sweeps" % bp},
+                            "kind": "oracle", "estimate": True,
+                            "sample": "each of %d samples: one BP sweep + 2 simple-update gates on "
+                                      "a random full-chi 127-qubit state; step estimated as 144 "
+                                      "gates + %.0f sweeps; steps = equivalent Floquet steps of "
+                                      "work timed" % (args.steps, bp)},
            "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -236,5 +236,9 @@ cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t s);
 // per edge.
 bool solve_refined_supported(int chi);
 cudaError_t launch_solve_refined(const SolveArgs& a, cudaStream_t s);
+// The two halves of launch_solve_refined: the FP64 Cholesky and the FP32
+// starting basis; the FP64 Newton step and leg matrices.
+cudaError_t launch_solve_refined_basis(const SolveArgs& a, cudaStream_t s);
+cudaError_t launch_solve_refined_newton(const SolveArgs& a, cudaStream_t s);
 
 }  // namespace tnbp

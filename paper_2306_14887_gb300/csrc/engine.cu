@@ -370,9 +370,9 @@ tn_status upload_plans(tn_handle* h) {
 }
 
 // ------------------------------------------------------------- profiling
-enum { P_BP = 0, P_NORM, P_ENV, P_SOLVE, P_REBUILD, P_COPY, P_PHYS, P_RHO, P_NCLS };
+enum { P_BP = 0, P_NORM, P_ENV, P_SOLVE, P_REBUILD, P_COPY, P_PHYS, P_RHO, P_REFINE, P_NCLS };
 const char* kProfNames[P_NCLS] = {"bp_contract", "bp_normalise", "gate_env", "trunc_solve",
-                                  "gate_rebuild", "copyback", "phys_gate", "rho"};
+                                  "gate_rebuild", "copyback", "phys_gate", "rho", "trunc_refine"};
 
 cudaEvent_t next_event(tn_handle* h) {
   if (h->ev_used == h->ev_pool.size()) {
@@ -1005,7 +1005,16 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
     if (kind == TN_SOLVE_REFINED) {
       a.max_sweeps = 20;
       a.orth_tol = h->cfg.solve_tol > 0 ? (float)h->cfg.solve_tol : 2e-6f;
-      TN_CUDA_TRY(launch_solve_refined(a, h->stream));
+      TN_CUDA_TRY(launch_solve_refined_basis(a, h->stream));
+      const double n = 2.0 * h->chi, x = h->chi;
+      // FP32 phase (Jacobi sweeps: about 7 of n^2/2 pairs x 16 n real flops)
+      prof_end(h, pi, 7.0 * n * n / 2 * 16.0 * n * a.n_edges, 0.0);
+      // FP64 phase: Newton step (Y, P: chi^3 each; Z, S, R and the update:
+      // n^2 chi each) and the leg matrices (2 chi^3), 8 real flops per cMAC
+      const int pr = prof_begin(h, P_REFINE);
+      TN_CUDA_TRY(launch_solve_refined_newton(a, h->stream));
+      prof_end(h, pr, 8.0 * (4.0 * x * x * x + 4.0 * n * n * x) * a.n_edges,
+               16.0 * (3.0 * n * n + n * x) * a.n_edges);
       h->stats.kernel_launches += 3;
     } else if (kind == TN_SOLVE_SHARED) {
       a.max_sweeps = 20;
@@ -1014,8 +1023,10 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
     } else {
       TN_CUDA_TRY(launch_solve(a, h->stream));
     }
-    const double n = 2.0 * h->chi;
-    prof_end(h, pi, 40.0 * n * n * n * a.n_edges, 4.0 * 16.0 * h->chi * h->chi * a.n_edges);
+    if (kind != TN_SOLVE_REFINED) {
+      const double n = 2.0 * h->chi;
+      prof_end(h, pi, 40.0 * n * n * n * a.n_edges, 4.0 * 16.0 * h->chi * h->chi * a.n_edges);
+    }
   }
   h->stats.kernel_launches++;
   h->mrt_valid = false;  // the solve rewrote the gate-edge messages

@@ -27,6 +27,10 @@
 
 #include "tnbp.h"
 
+namespace tnbp {
+void set_error(const std::string& msg);  // the thread-local tn_last_error text (engine.cu)
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -45,6 +49,7 @@ struct Job {
   tn_status status = TN_EAGAIN;
   int32_t steps_done = 0;
   std::vector<double> z;
+  std::string error;  // the worker's error message when status is an error
 };
 
 void* slot_alloc(size_t bytes, void*, void* stream) {
@@ -99,6 +104,7 @@ void tn_server::run_slot() {
       job->t_admit = Clock::now();
     }
     tn_status status = TN_ECUDA;
+    std::string err = dev_ok ? "" : "cudaSetDevice or cudaStreamCreate failed for the slot";
     int32_t done_steps = 0;
     std::vector<double> z(job->n, 0.0);
     if (dev_ok) {
@@ -115,12 +121,16 @@ void tn_server::run_slot() {
           const tn_status zs = tn_expect_z_all(h, z.data());
           if (zs != TN_OK) status = zs;
         }
+        if (status != TN_OK && status != TN_ENOTCONVERGED) err = tn_last_error();
         tn_destroy(h);
+      } else {
+        err = tn_last_error();
       }
     }
     {
       std::lock_guard<std::mutex> lk(mu);
       job->status = status;
+      job->error = err;
       job->steps_done = done_steps;
       job->z.swap(z);
       job->t_done = Clock::now();
@@ -209,6 +219,8 @@ static tn_status take_result(tn_server* s, std::unordered_map<uint64_t, std::sha
     info->latency_s = std::chrono::duration<double>(j.t_done - j.t_submit).count();
   }
   const tn_status status = j.status;
+  // the message was set on the worker's thread; repeat it on the caller's
+  if (status != TN_OK && status != TN_ENOTCONVERGED) tnbp::set_error(j.error);
   s->jobs.erase(it);
   return status;
 }

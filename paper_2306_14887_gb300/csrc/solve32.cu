@@ -26,6 +26,8 @@
 //      messages <- diag(S).
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "tnbp.h"
 
@@ -895,10 +897,16 @@ bool solve32_supported(int chi) { return chi >= 1 && chi <= kMaxChi; }
 cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t st) {
   if (a.n_edges <= 0) return cudaSuccess;
   if (!solve32_supported(a.chi)) return cudaErrorInvalidValue;
+  // the shared-memory limit is raised once, to the largest chi's need, so that
+  // concurrent launches at different chi (the job server) never lower it
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(solve32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes(kMaxChi));
+  });
+  if (attr != cudaSuccess) return attr;
   const size_t sm = smem_bytes(a.chi);
-  cudaError_t e = cudaFuncSetAttribute(solve32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
   solve32_kernel<<<a.n_edges, kThreads, sm, st>>>(a);
   return cudaGetLastError();
 }

@@ -47,6 +47,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "tnbp.h"
@@ -75,9 +76,6 @@ __device__ __forceinline__ void cfma(cd& acc, cd a, cd b) {
 __device__ __forceinline__ double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
 __device__ __forceinline__ cd shfl_xor(cd v, int o) {
   return {__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
-}
-__device__ __forceinline__ cd shfl_idx(cd v, int src) {
-  return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
 }
 
 constexpr int kThreads = 256;
@@ -176,8 +174,10 @@ __device__ void pivoted_cholesky64(cd* A, int m, int ld, int* perm, double rel_t
       const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
       const cd li = A[i * ld + k], lj = A[j * ld + k];
       cd v = A[i * ld + j];
-      v.x -= li.x * lj.x + li.y * lj.y;
-      v.y -= li.y * lj.x - li.x * lj.y;
+      v.x = fma(-li.x, lj.x, v.x);
+      v.x = fma(-li.y, lj.y, v.x);
+      v.y = fma(-li.y, lj.x, v.y);
+      v.y = fma(li.x, lj.y, v.y);
       A[i * ld + j] = v;
     }
     __syncthreads();
@@ -515,23 +515,25 @@ __global__ void __launch_bounds__(kThreads, 1) refine_kernel(SolveArgs a, int cw
 // ------------------------------------------------------------ leg matrices
 // Same split of the kept-column slots.  Per edge: the kept set (the chi
 // candidates with sigma above svd_cut * the largest), ||sigma||, and each
-// column's slot in decreasing order; per column m (one warp), both blocks b:
-//   C_v: solve L_b^H w = u_b, D_v[b][perm_b[s]][pos] = w[s] sqrt(sigma / ||sigma||)
-//   C_w: y = L_b u_b, D_w[q][perm_b[t]][pos] += b_b(q) conj(y[t]) / sqrt(sigma ||sigma||)
+// column's slot in decreasing order.  Per chunk of refined columns u (both
+// blocks b), in FP64:
+//   Y = L_b u_b          (R_v^H u, so that C_w = R_v^T conj(u) = conj(Y)), and
+//   W with L_b^H W = u_b (back substitution: C_v = R_v^+ u),
+// then D_v[b][perm_b[s]][pos] = W[(b, s)] sqrt(sigma / ||sigma||) and
+// D_w[q][e][pos] = sum_b b_b(q) conj(Y[(b, pinv_b(e))]) / sqrt(sigma ||sigma||)
 // with b_b(q) = exp(s i pi/4 s_b s_q), as the gate split gives.
-__global__ void __launch_bounds__(kThreads) legs_kernel(SolveArgs a) {
-  constexpr int kH = kMaxChi / 32;
+__global__ void __launch_bounds__(kThreads, 1) legs_kernel(SolveArgs a, int cwmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* Lsh = reinterpret_cast<cd*>(smem_raw);                       // [2][chi][chi]
-  double* dinv = reinterpret_cast<double*>(Lsh + 2 * (int64_t)a.chi * a.chi);  // [2][chi]
-  __shared__ double lam_s[kMaxChi];
-  __shared__ int pos_s[kMaxChi];
-  __shared__ unsigned char keep_s[kMaxChi];
-  __shared__ double scal[4];  // nrm, smax, kept count, discarded weight
-  __shared__ cd dwcol[kWarps][2][kMaxChi];  // D_w[q][e] of the warp's column
   const int chi = a.chi, n = 2 * chi;
+  cd* Ub = reinterpret_cast<cd*>(smem_raw);        // [cwmax][n] refined columns
+  cd* Yb = Ub + (int64_t)cwmax * n;                // [cwmax][n]
+  double* lam_s = reinterpret_cast<double*>(Yb + (int64_t)cwmax * n);  // [chi]
+  int* pos_s = reinterpret_cast<int*>(lam_s + chi);                     // [chi]
+  int* pinv = pos_s + chi;                                             // [2][chi]
+  unsigned char* keep_s = reinterpret_cast<unsigned char*>(pinv + 2 * chi);  // [chi]
+  __shared__ double scal[4];  // nrm, smax, kept count, discarded weight
   const int64_t c2 = (int64_t)chi * chi;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t T = (int64_t)a.n_edges * chi;
   const int64_t g0 = (int64_t)blockIdx.x * T / gridDim.x;
   const int64_t g1 = (int64_t)(blockIdx.x + 1) * T / gridDim.x;
@@ -544,11 +546,7 @@ __global__ void __launch_bounds__(kThreads) legs_kernel(SolveArgs a) {
     const EdgeView v = edge_view(a, e);
     const int cand = min(chi, v.act);
     for (int m = tid; m < chi; m += blockDim.x) lam_s[m] = m < cand ? v.lam1[m] : 0.0;
-    for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) Lsh[idx] = v.L[idx];
-    for (int t = tid; t < 2 * chi; t += blockDim.x) {
-      const double d = v.L[(int64_t)(t / chi) * c2 + (int64_t)(t % chi) * (chi + 1)].x;
-      dinv[t] = d > 0.0 ? 1.0 / d : 0.0;
-    }
+    for (int i = tid; i < 2 * chi; i += blockDim.x) pinv[(i / chi) * chi + v.perm[i]] = i % chi;
     __syncthreads();
     if (tid == 0) {
       double smax = 0.0;
@@ -581,7 +579,6 @@ __global__ void __launch_bounds__(kThreads) legs_kernel(SolveArgs a) {
       }
       pos_s[m] = p;
     }
-    __syncthreads();
     const double nrm = scal[0];
     const bool ok = nrm > 0.0 && isfinite(nrm);
     if (j0 == 0 && tid == 0) {
@@ -593,102 +590,126 @@ __global__ void __launch_bounds__(kThreads) legs_kernel(SolveArgs a) {
     }
     float* dv = a.dmat + (int64_t)e * 8 * c2;
     float* dw = dv + 4 * c2;
-    for (int m = j0 + warp; m < j1; m += kWarps) {
-      const int p = pos_s[m];
-      const bool keep = ok && keep_s[m];
-      const double sgm = keep ? sqrt(lam_s[m]) : 0.0;
-      const double fv = keep ? sqrt(sgm / nrm) : 0.0;
-      const double fw = keep ? 1.0 / sqrt(sgm * nrm) : 0.0;
-      for (int b = 0; b < 2; ++b) {
-        const int rb = v.rank[b];
-        const cd* Lb = Lsh + b * c2;
-        const double* db = dinv + b * chi;
-        const int* pb = v.perm + b * chi;
-        cd u[kH];
-#pragma unroll
-        for (int h = 0; h < kH; ++h) {
-          const int t = h * 32 + lane;
-          u[h] = (keep && t < chi) ? v.U1[(int64_t)m * n + b * chi + t] : cz();
-        }
-        // back-substitution for L_b^H w = u over t < rank_b, from the last
-        cd w[kH], uu[kH];
-#pragma unroll
-        for (int h = 0; h < kH; ++h) { w[h] = cz(); uu[h] = u[h]; }
-        for (int t = rb - 1; t >= 0; --t) {
-          cd ut = cz();
-#pragma unroll
-          for (int h = 0; h < kH; ++h)
-            if ((t >> 5) == h) ut = shfl_idx(uu[h], t & 31);
-          const cd wt = cscale(ut, db[t]);
-#pragma unroll
-          for (int h = 0; h < kH; ++h) {
-            const int t2 = h * 32 + lane;
-            if (t2 == t) w[h] = wt;
-            if (t2 < t) uu[h] = csub(uu[h], cmul(cconj(Lb[(int64_t)t * chi + t2]), wt));
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < kH; ++h) {
-          const int s = h * 32 + lane;
-          if (s < chi) {
-            const cd z = (s < rb) ? cscale(w[h], fv) : cz();
-            const int64_t o = (int64_t)b * 2 * c2 + (int64_t)pb[s] * chi + p;
-            dv[o] = (float)z.x;
-            dv[o + c2] = (float)z.y;
-          }
-        }
-        // y[t] = sum_{i <= t} L_b[t][i] u[i]
-        cd y[kH];
-#pragma unroll
-        for (int h = 0; h < kH; ++h) y[h] = cz();
-        for (int i = 0; i < chi; ++i) {
-          cd ui = cz();
-#pragma unroll
-          for (int h = 0; h < kH; ++h)
-            if ((i >> 5) == h) ui = shfl_idx(u[h], i & 31);
-#pragma unroll
-          for (int h = 0; h < kH; ++h) {
-            const int t = h * 32 + lane;
-            if (t < chi && i <= t) cfma(y[h], Lb[(int64_t)t * chi + i], ui);
-          }
-        }
-        const double sb = (b == 0) ? 1.0 : -1.0;
-        const cd b0 = {c45, sg * sb * c45}, b1 = {c45, -sg * sb * c45};
-#pragma unroll
-        for (int h = 0; h < kH; ++h) {
-          const int t = h * 32 + lane;
-          if (t < chi) {
-            const cd cwv = {y[h].x * fw, -y[h].y * fw};
-            const int ei = pb[t];
-            // the b = 0 pass assigns every entry e once (perm is a permutation)
-            dwcol[warp][0][ei] = b == 0 ? cmul(b0, cwv) : cadd(dwcol[warp][0][ei], cmul(b0, cwv));
-            dwcol[warp][1][ei] = b == 0 ? cmul(b1, cwv) : cadd(dwcol[warp][1][ei], cmul(b1, cwv));
-          }
-        }
-        __syncwarp();
+    for (int js = j0; js < j1; js += cwmax) {
+      const int cw = min(cwmax, j1 - js);
+      for (int idx = tid; idx < cw * n; idx += blockDim.x) {
+        const int jj = idx / n;
+        Ub[idx] = keep_s[js + jj] ? v.U1[(int64_t)js * n + idx] : cz();
       }
-      for (int idx = lane; idx < 2 * chi; idx += 32) {
-        const int q = idx / chi, ei = idx - q * chi;
-        const cd val = dwcol[warp][q][ei];
-        const int64_t o = (int64_t)q * 2 * c2 + (int64_t)ei * chi + p;
-        dw[o] = (float)val.x;
-        dw[o + c2] = (float)val.y;
+      __syncthreads();
+      // Y = L_b u_b (from the unmodified columns) first
+      rows8(
+          n, cw, Ub, n,
+          [&](int i, int& lo, int& hi) {
+            const int b = i / chi, t = i - b * chi;
+            lo = 0;
+            hi = min(t + 1, v.rank[b]);
+          },
+          [&](int i, int k) {
+            const int b = i / chi, t = i - b * chi;
+            return v.L[b * c2 + (int64_t)t * chi + k];
+          },
+          [&](int i, int k) { return (i / chi) * chi + k; },
+          [&](int i, int j, cd val) { Yb[j * n + i] = val; });
+      __syncthreads();
+      // W: solve L_b^H w = u_b for every column of the chunk by back
+      // substitution over s = rank_b - 1 .. 0, in place in Ub: w[s] = u[s] /
+      // L[s][s], then u[t] -= conj(L[s][t]) w[s] for t < s (both blocks and all
+      // columns at once, one pass per s)
+      const int rmax = max(v.rank[0], v.rank[1]);
+      for (int sidx = rmax - 1; sidx >= 0; --sidx) {
+        for (int idx = tid; idx < 2 * cw; idx += blockDim.x) {
+          const int b = idx / cw, jj = idx - b * cw;
+          if (sidx < v.rank[b]) {
+            const cd d = v.L[b * c2 + (int64_t)sidx * chi + sidx];
+            Ub[jj * n + b * chi + sidx] = cscale(Ub[jj * n + b * chi + sidx], 1.0 / d.x);
+          }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < 2 * cw * sidx; idx += blockDim.x) {
+          const int b = idx / (cw * sidx), rem = idx - b * cw * sidx;
+          const int jj = rem / sidx, t = rem - jj * sidx;
+          if (sidx < v.rank[b]) {
+            const cd l = cconj(v.L[b * c2 + (int64_t)sidx * chi + t]);
+            const cd w = Ub[jj * n + b * chi + sidx];
+            cd& u = Ub[jj * n + b * chi + t];
+            u.x = fma(-l.x, w.x, u.x);
+            u.x = fma(l.y, w.y, u.x);
+            u.y = fma(-l.x, w.y, u.y);
+            u.y = fma(-l.y, w.x, u.y);
+          }
+        }
+        __syncthreads();
       }
-      __syncwarp();
-      if (lane == 0 && a.s_out) a.s_out[(int64_t)e * chi + p] = keep ? sgm / nrm : 0.0;
+      cd* Wb_ = Ub;  // W now occupies Ub (entries past each block's rank unused)
+      // D_v and D_w columns, one thread per (column, e)
+      for (int idx = tid; idx < cw * chi; idx += blockDim.x) {
+        const int jj = idx / chi, ei = idx - jj * chi, m = js + jj;
+        const int p = pos_s[m];
+        const bool keep = ok && keep_s[m];
+        const double sgm = keep ? sqrt(lam_s[m]) : 0.0;
+        const double fv = keep ? sqrt(sgm / nrm) : 0.0;
+        const double fw = keep ? 1.0 / sqrt(sgm * nrm) : 0.0;
+        const int64_t o = (int64_t)ei * chi + p;
+        cd w0 = cz(), w1 = cz();
+        for (int b = 0; b < 2; ++b) {
+          const int s = pinv[b * chi + ei];
+          const cd z = (keep && s < v.rank[b]) ? cscale(Wb_[jj * n + b * chi + s], fv) : cz();
+          dv[(int64_t)b * 2 * c2 + o] = (float)z.x;
+          dv[(int64_t)b * 2 * c2 + c2 + o] = (float)z.y;
+          const cd y = Yb[jj * n + b * chi + s];
+          const cd cwv = {y.x * fw, -y.y * fw};
+          const double sb = (b == 0) ? 1.0 : -1.0;
+          w0 = cadd(w0, cmul({c45, sg * sb * c45}, cwv));
+          w1 = cadd(w1, cmul({c45, -sg * sb * c45}, cwv));
+        }
+        dw[o] = (float)w0.x;
+        dw[c2 + o] = (float)w0.y;
+        dw[2 * c2 + o] = (float)w1.x;
+        dw[3 * c2 + o] = (float)w1.y;
+      }
+      for (int jj = tid; jj < cw; jj += blockDim.x) {
+        const int m = js + jj, p = pos_s[m];
+        const bool keep = ok && keep_s[m];
+        if (a.s_out) a.s_out[(int64_t)e * chi + p] = keep ? sqrt(lam_s[m]) / nrm : 0.0;
+      }
       if (ok && a.msg) {
         float* m0 = a.msg + (int64_t)a.msg_vw[2 * e] * 2 * c2;
         float* m1 = a.msg + (int64_t)a.msg_vw[2 * e + 1] * 2 * c2;
-        const float val = keep ? (float)(sgm / nrm) : 0.f;
-        for (int k = lane; k < chi; k += 32) {
-          const float x = (k == p) ? val : 0.f;
-          m0[(int64_t)p * chi + k] = x; m0[c2 + (int64_t)p * chi + k] = 0.f;
-          m1[(int64_t)p * chi + k] = x; m1[c2 + (int64_t)p * chi + k] = 0.f;
+        for (int idx = tid; idx < cw * chi; idx += blockDim.x) {
+          const int jj = idx / chi, k = idx - jj * chi, m = js + jj;
+          const int p = pos_s[m];
+          const float val = (k == p && keep_s[m]) ? (float)(sqrt(lam_s[m]) / nrm) : 0.f;
+          m0[(int64_t)p * chi + k] = val; m0[c2 + (int64_t)p * chi + k] = 0.f;
+          m1[(int64_t)p * chi + k] = val; m1[c2 + (int64_t)p * chi + k] = 0.f;
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
+}
+
+// Shared-memory limits of the refined solve's kernels, raised once to the
+// largest request any chi <= kMaxChi makes, so that concurrent launches (the
+// job server's slots) never lower a limit another thread relies on.
+constexpr size_t kCholSmemMax = sizeof(cd) * kMaxChi * (kMaxChi + 1);
+constexpr size_t kRefineSmemMax = kSmemBudget + 4096;
+constexpr size_t kLegsSmemMax = kSmemBudget / 2 + 8192;
+
+cudaError_t refine_prepare() {
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] {
+    result = cudaFuncSetAttribute(chol64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kCholSmemMax);
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kRefineSmemMax);
+    if (result == cudaSuccess)
+      result = cudaFuncSetAttribute(legs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kLegsSmemMax);
+  });
+  return result;
 }
 
 int sm_count() {
@@ -702,21 +723,26 @@ int sm_count() {
 
 bool solve_refined_supported(int chi) { return chi >= 1 && chi <= kMaxChi && solve32_supported(chi); }
 
-cudaError_t launch_solve_refined(const SolveArgs& a, cudaStream_t st) {
+cudaError_t launch_solve_refined_basis(const SolveArgs& a, cudaStream_t st) {
   if (a.n_edges <= 0) return cudaSuccess;
   if (!solve_refined_supported(a.chi)) return cudaErrorInvalidValue;
-  const int chi = a.chi, n = 2 * chi;
-  // 1. FP64 Cholesky of the v-side Gram blocks
+  const int chi = a.chi;
+  // 1. FP64 Cholesky of the v-side Gram blocks, conj(G_w) in FP64
   const size_t sm_chol = sizeof(cd) * (size_t)chi * (chi + 1);
-  cudaError_t e = cudaFuncSetAttribute(chol64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm_chol);
+  cudaError_t e = refine_prepare();
   if (e != cudaSuccess) return e;
   chol64_kernel<<<dim3(2, a.n_edges), kThreads, sm_chol, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // 2. FP32 starting basis
   SolveArgs b = a;
   b.basis = 1;
-  if ((e = launch_solve32(b, st)) != cudaSuccess) return e;
+  return launch_solve32(b, st);
+}
+
+cudaError_t launch_solve_refined_newton(const SolveArgs& a, cudaStream_t st) {
+  if (a.n_edges <= 0) return cudaSuccess;
+  if (!solve_refined_supported(a.chi)) return cudaErrorInvalidValue;
+  const int chi = a.chi, n = 2 * chi;
   // 3. FP64 Newton step, the kept-column slots balanced over the SMs
   const int64_t T = (int64_t)a.n_edges * chi;
   const int cw_fit = (int)(kSmemBudget / (sizeof(cd) * 4 * (size_t)n + 2 * sizeof(double)));
@@ -724,16 +750,23 @@ cudaError_t launch_solve_refined(const SolveArgs& a, cudaStream_t st) {
   grid = (int)std::max<int64_t>(grid, (T + cw_fit - 1) / cw_fit);
   const int cwmax = (int)((T + grid - 1) / grid);
   const size_t sm_ref = sizeof(cd) * 4 * (size_t)cwmax * n + 2 * sizeof(double) * cwmax;
-  e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ref);
+  cudaError_t e = refine_prepare();
   if (e != cudaSuccess) return e;
+  if (sm_ref > kRefineSmemMax) return cudaErrorInvalidValue;
   refine_kernel<<<grid, kThreads, sm_ref, st>>>(a, cwmax);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // 4. FP64 leg matrices, spectrum and messages
-  const size_t sm_legs = sizeof(cd) * 2 * (size_t)chi * chi + sizeof(double) * 2 * chi;
-  e = cudaFuncSetAttribute(legs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_legs);
-  if (e != cudaSuccess) return e;
-  legs_kernel<<<grid, kThreads, sm_legs, st>>>(a);
+  const size_t sm_legs = sizeof(cd) * 2 * (size_t)cwmax * n + sizeof(double) * chi +
+                         sizeof(int) * 3 * chi + chi + 16;
+  if (sm_legs > kLegsSmemMax) return cudaErrorInvalidValue;
+  legs_kernel<<<grid, kThreads, sm_legs, st>>>(a, cwmax);
   return cudaGetLastError();
+}
+
+cudaError_t launch_solve_refined(const SolveArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_solve_refined_basis(a, st);
+  if (e != cudaSuccess) return e;
+  return launch_solve_refined_newton(a, st);
 }
 
 }  // namespace tnbp

@@ -77,3 +77,5 @@ def test_reference_arm_prints_one_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # bounded samples: labelled an estimate, steps = the Floquet steps of work timed
+    assert d["estimate"] is True and d["samples"] == 1 and 0 < d["steps"] <= 1.5
