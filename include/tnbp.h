@@ -451,6 +451,10 @@ typedef struct {
   tn_config cfg;       /* chi, precision, tolerances as for tn_create */
   double theta_h;
   int32_t steps;
+  const tn_pauli* ops; /* weight-k strings evaluated after the steps, as tn_expect
+                          evaluates them (copied at submit; may be NULL) */
+  int32_t n_ops;       /* number of strings (0: <Z_v> only) */
+  int32_t ops_method;  /* tn_expect's method: 0 BP region, 1 extended evolution */
 } tn_job;
 
 typedef struct {
@@ -480,6 +484,14 @@ tn_status tn_server_poll(tn_server* s, uint64_t ticket, double* z, tn_result* in
 /* tn_server_wait — tn_server_poll after waiting up to timeout_s seconds. */
 tn_status tn_server_wait(tn_server* s, uint64_t ticket, double timeout_s, double* z,
                          tn_result* info);
+/* tn_server_poll_ex / tn_server_wait_ex — as tn_server_poll / tn_server_wait,
+ * and ops_out (caller-owned, the job's n_ops doubles, may be NULL) receives the
+ * values of the job's strings (Main text, "Measuring expectation values"), in
+ * the order submitted. */
+tn_status tn_server_poll_ex(tn_server* s, uint64_t ticket, double* z, double* ops_out,
+                            tn_result* info);
+tn_status tn_server_wait_ex(tn_server* s, uint64_t ticket, double timeout_s, double* z,
+                            double* ops_out, tn_result* info);
 tn_status tn_server_get_stats(tn_server* s, tn_server_stats* out);
 /* tn_server_destroy — drop queued jobs, wait for the resident ones, join the slots. */
 tn_status tn_server_destroy(tn_server* s);

@@ -33,6 +33,7 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_truncation_solve_noalloc", "tn_truncation_solve_ex", "tn_last_error",
            "tn_version", "tn_apply_floquet_field", "tn_server_create", "tn_server_submit",
            "tn_server_poll", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
+           "tn_server_poll_ex", "tn_server_wait_ex",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
            "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma",
            "tn_bp_error", "tn_graph_info", "tn_selftest_bounded_wait"]
@@ -90,7 +91,8 @@ class tn_server_config(C.Structure):
 
 class tn_job(C.Structure):
     _fields_ = [("graph", tn_graph), ("cfg", tn_config), ("theta_h", C.c_double),
-                ("steps", C.c_int32)]
+                ("steps", C.c_int32), ("ops", C.c_void_p), ("n_ops", C.c_int32),
+                ("ops_method", C.c_int32)]
 
 
 class tn_result(C.Structure):
@@ -154,6 +156,8 @@ def lib():
         L.tn_server_submit.argtypes = [vp, C.POINTER(tn_job), C.POINTER(C.c_uint64)]
         L.tn_server_poll.argtypes = [vp, C.c_uint64, dp, C.POINTER(tn_result)]
         L.tn_server_wait.argtypes = [vp, C.c_uint64, C.c_double, dp, C.POINTER(tn_result)]
+        L.tn_server_poll_ex.argtypes = [vp, C.c_uint64, dp, dp, C.POINTER(tn_result)]
+        L.tn_server_wait_ex.argtypes = [vp, C.c_uint64, C.c_double, dp, dp, C.POINTER(tn_result)]
         L.tn_server_get_stats.argtypes = [vp, C.POINTER(tn_server_stats)]
         L.tn_server_destroy.argtypes = [vp]
         L.tn_chi_extrapolate.argtypes = [dp, dp, i32, i32, dp, dp, dp]
@@ -509,37 +513,58 @@ class Server:
         self._n = {}
 
     def submit(self, n, edges, colours, chi, theta, steps, prec="fp32", bp_tol=1e-10,
-               bp_max_iters=1000, svd_cutoff=0.0, solve="auto"):
+               bp_max_iters=1000, svd_cutoff=0.0, solve="auto", ops=None, method=0):
+        """Queue a job; ops: optional list of (dict {site: 'X'|'Y'|'Z'}, sign)
+        strings evaluated after the steps by tn_expect's method (0 region, 1
+        extended evolution); their values come back in info["ops"]."""
         g, keep = _graph_struct(n, edges, colours)
         job = tn_job()
         job.graph = g
         job.cfg = _config(chi, prec, bp_tol, bp_max_iters, svd_cutoff, solve)
         job.theta_h = float(theta)
         job.steps = int(steps)
+        ops = list(ops or [])
+        arr = (tn_pauli * max(1, len(ops)))()
+        hold = []
+        for i, (o, sign) in enumerate(ops):
+            sites = np.array(sorted(o), dtype=np.int32)
+            labels = "".join(o[int(q)] for q in sites).encode()
+            hold.append((sites, labels))
+            arr[i].weight = len(sites)
+            arr[i].sites = sites.ctypes.data_as(C.POINTER(C.c_int32))
+            arr[i].paulis = labels
+            arr[i].sign = int(sign)
+        job.ops = C.cast(arr, C.c_void_p) if ops else None
+        job.n_ops = len(ops)
+        job.ops_method = int(method)
         t = C.c_uint64()
         _check(lib().tn_server_submit(self._h, C.byref(job), C.byref(t)))
-        del keep
-        self._n[t.value] = int(n)
+        del keep, hold
+        self._n[t.value] = (int(n), len(ops))
         return t.value
 
     def _take(self, fn, ticket, *extra):
-        z = np.zeros(self._n[ticket], dtype=np.float64)
+        n, n_ops = self._n[ticket]
+        z = np.zeros(n, dtype=np.float64)
+        vals = np.zeros(max(1, n_ops), dtype=np.float64)
         info = tn_result()
         st = fn(self._h, C.c_uint64(ticket), *extra,
-                z.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info))
+                z.ctypes.data_as(C.POINTER(C.c_double)),
+                vals.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info))
         if st == -7:  # TN_EAGAIN
             return None
         del self._n[ticket]
         _check(st if st != -3 else 0)
         return z, {"status": info.status, "steps_done": info.steps_done,
-                   "queue_s": info.queue_s, "latency_s": info.latency_s}
+                   "queue_s": info.queue_s, "latency_s": info.latency_s,
+                   "ops": vals[:n_ops].copy()}
 
     def poll(self, ticket):
         """None while queued or running, else (<Z_v> array, info dict)."""
-        return self._take(lib().tn_server_poll, ticket)
+        return self._take(lib().tn_server_poll_ex, ticket)
 
     def wait(self, ticket, timeout=600.0):
-        return self._take(lib().tn_server_wait, ticket, C.c_double(timeout))
+        return self._take(lib().tn_server_wait_ex, ticket, C.c_double(timeout))
 
     def stats(self):
         s = tn_server_stats()

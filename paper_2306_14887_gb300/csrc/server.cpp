@@ -50,6 +50,12 @@ struct Job {
   int32_t steps_done = 0;
   std::vector<double> z;
   std::string error;  // the worker's error message when status is an error
+  // the job's strings (deep copies of the submitted tn_pauli array)
+  std::vector<std::vector<int32_t>> op_sites;
+  std::vector<std::string> op_labels;
+  std::vector<int8_t> op_signs;
+  int32_t ops_method = 0;
+  std::vector<double> op_values;
 };
 
 void* slot_alloc(size_t bytes, void*, void* stream) {
@@ -106,7 +112,7 @@ void tn_server::run_slot() {
     tn_status status = TN_ECUDA;
     std::string err = dev_ok ? "" : "cudaSetDevice or cudaStreamCreate failed for the slot";
     int32_t done_steps = 0;
-    std::vector<double> z(job->n, 0.0);
+    std::vector<double> z(job->n, 0.0), op_vals;
     if (dev_ok) {
       tn_graph g{job->n, (int32_t)(job->edges.size() / 2), job->edges.data(),
                  job->has_colours ? job->colours.data() : nullptr, 0};
@@ -121,6 +127,20 @@ void tn_server::run_slot() {
           const tn_status zs = tn_expect_z_all(h, z.data());
           if (zs != TN_OK) status = zs;
         }
+        if ((status == TN_OK || status == TN_ENOTCONVERGED) && !job->op_signs.empty()) {
+          const size_t n_ops = job->op_signs.size();
+          std::vector<tn_pauli> ops(n_ops);
+          for (size_t k = 0; k < n_ops; ++k) {
+            ops[k].weight = (int32_t)job->op_sites[k].size();
+            ops[k].sites = job->op_sites[k].data();
+            ops[k].paulis = job->op_labels[k].c_str();
+            ops[k].sign = job->op_signs[k];
+          }
+          op_vals.assign(n_ops, 0.0);
+          const tn_status os =
+              tn_expect(h, ops.data(), (int32_t)n_ops, job->ops_method, op_vals.data());
+          if (os != TN_OK) status = os;
+        }
         if (status != TN_OK && status != TN_ENOTCONVERGED) err = tn_last_error();
         tn_destroy(h);
       } else {
@@ -131,6 +151,7 @@ void tn_server::run_slot() {
       std::lock_guard<std::mutex> lk(mu);
       job->status = status;
       job->error = err;
+      job->op_values.swap(op_vals);
       job->steps_done = done_steps;
       job->z.swap(z);
       job->t_done = Clock::now();
@@ -193,6 +214,17 @@ tn_status tn_server_submit(tn_server* s, const tn_job* job, uint64_t* ticket) {
   j->theta = job->theta_h;
   j->steps = job->steps;
   j->footprint = fp;
+  if (job->n_ops < 0 || (job->n_ops > 0 && !job->ops) ||
+      (job->n_ops > 0 && job->ops_method != 0 && job->ops_method != 1))
+    return TN_EINVAL;
+  j->ops_method = job->ops_method;
+  for (int32_t k = 0; k < job->n_ops; ++k) {
+    const tn_pauli& p = job->ops[k];
+    if (p.weight < 1 || !p.sites || !p.paulis) return TN_EINVAL;
+    j->op_sites.emplace_back(p.sites, p.sites + p.weight);
+    j->op_labels.emplace_back(p.paulis, p.paulis + p.weight);
+    j->op_signs.push_back(p.sign);
+  }
   j->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -208,9 +240,12 @@ tn_status tn_server_submit(tn_server* s, const tn_job* job, uint64_t* ticket) {
 }
 
 static tn_status take_result(tn_server* s, std::unordered_map<uint64_t, std::shared_ptr<Job>>::iterator it,
-                             double* z, tn_result* info) {
+                             double* z, double* ops_out, tn_result* info) {
   Job& j = *it->second;
   if (z) for (int32_t i = 0; i < j.n; ++i) z[i] = j.z.empty() ? 0.0 : j.z[i];
+  if (ops_out)
+    for (size_t k = 0; k < j.op_signs.size(); ++k)
+      ops_out[k] = k < j.op_values.size() ? j.op_values[k] : 0.0;
   if (info) {
     info->status = j.status;
     info->n_vertices = j.n;
@@ -225,17 +260,27 @@ static tn_status take_result(tn_server* s, std::unordered_map<uint64_t, std::sha
   return status;
 }
 
-tn_status tn_server_poll(tn_server* s, uint64_t ticket, double* z, tn_result* info) {
+tn_status tn_server_poll_ex(tn_server* s, uint64_t ticket, double* z, double* ops_out,
+                            tn_result* info) {
   if (!s) return TN_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->jobs.find(ticket);
   if (it == s->jobs.end()) return TN_EINVAL;
   if (it->second->status == TN_EAGAIN) return TN_EAGAIN;
-  return take_result(s, it, z, info);
+  return take_result(s, it, z, ops_out, info);
+}
+
+tn_status tn_server_poll(tn_server* s, uint64_t ticket, double* z, tn_result* info) {
+  return tn_server_poll_ex(s, ticket, z, nullptr, info);
 }
 
 tn_status tn_server_wait(tn_server* s, uint64_t ticket, double timeout_s, double* z,
                          tn_result* info) {
+  return tn_server_wait_ex(s, ticket, timeout_s, z, nullptr, info);
+}
+
+tn_status tn_server_wait_ex(tn_server* s, uint64_t ticket, double timeout_s, double* z,
+                            double* ops_out, tn_result* info) {
   if (!s) return TN_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->jobs.find(ticket);
@@ -250,7 +295,7 @@ tn_status tn_server_wait(tn_server* s, uint64_t ticket, double timeout_s, double
   }
   it = s->jobs.find(ticket);
   if (it == s->jobs.end()) return TN_EINVAL;  // taken by a concurrent poll
-  return take_result(s, it, z, info);
+  return take_result(s, it, z, ops_out, info);
 }
 
 tn_status tn_server_get_stats(tn_server* s, tn_server_stats* out) {

@@ -12,6 +12,7 @@ from oracle import bptn as OB
 from oracle import clifford as OC
 from oracle import graph as OG
 from oracle import statevector as OS
+from test_gpu_headline import check_valid_state
 from workloads import THETA_SMALL, random_state
 
 pytestmark = pytest.mark.gpu
@@ -106,7 +107,7 @@ def test_ring12_floquet_matches_oracle(tnlib, theta):
     if o.min_gap > 1e-6:
         assert np.abs(z - o.all_z()).max() < Z_TOL
     else:
-        assert np.all(np.abs(z) <= 1 + 1e-6)
+        check_valid_state(s, g, 2e-6)
     if theta == 0.0:
         assert np.abs(z - 1.0).max() < Z_TOL
     s.close()
@@ -216,7 +217,9 @@ def test_eagle127_deeper_truncated_matches_oracle(tnlib, chi, steps, theta):
     if o.min_gap > 1e-6:
         assert np.abs(z - o.all_z()).max() < Z_TOL
     else:
-        assert np.abs(z - o.all_z()).max() < 1e-3
+        # a near-tie at a truncation: several results are correct, so only what
+        # every valid result has is checked
+        check_valid_state(s, g, 2e-6)
     s.close()
 
 

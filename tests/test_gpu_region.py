@@ -97,3 +97,35 @@ def test_region_tensor_core_modes(tnlib, prec, tol):
         got = s.expect([(ops, 1) for ops in strings], method=0)
     want = np.array([o.region_expectation(ops).real for ops in strings])
     assert np.abs(got - want).max() < tol
+
+
+def weight17_generator(g, nprime=5):
+    """The first qubit i (in increasing order) whose string
+    U^n'(pi/2) Z_i U^n'(pi/2)^dagger has weight 17, for the extended-evolution
+    depth n' = 5 of the printed weight-10 string: the reading of the weight-17
+    observable, whose support the paper does not print."""
+    for i in range(g.n):
+        s = OC.string_from_z(g, i, nprime)
+        if len(s.ops) == 17:
+            return i, s
+    raise AssertionError("no weight-17 string")
+
+
+def test_weight17_string_both_methods_match_oracle(tnlib):
+    """A weight-17 string on 127 qubits after 5 steps (chi = 8, truncating from
+    step 4), by the BP region (method 0) and by extended evolution (method 1),
+    each against the oracle's same method ("Measuring expectation values")."""
+    g = OG.eagle127()
+    site, s17 = weight17_generator(g)
+    ops = dict(s17.ops)
+    assert (site, len(ops)) == (9, 17)
+    chi, theta, steps = 8, 0.4, 5
+    o = OB.run(g, chi, theta, steps)
+    want_region = o.region_expectation(ops).real
+    want_ext, _ = OB.extended_string_expectation(o, site, 5)
+    with tnlib.TNState(g.n, g.edges, g.colours, chi=chi) as s:
+        s.apply_floquet(theta, steps)
+        got_region = s.expect([(ops, 1)], method=0)[0]
+        got_ext = s.expect([(ops, 1)], method=1)[0]
+    assert abs(got_region - want_region) < 1e-6
+    assert abs(got_ext - want_ext) < 1e-6

@@ -101,3 +101,26 @@ def test_theta_chi_sweep_extrapolates_to_the_oracle(tnlib):
     assert np.abs(out["slope"][1]).max() < 1e-4
     # the intercepts are the straight line through the two chi points
     assert np.allclose(out["z_inf"], 2 * out["z"][:, 1] - out["z"][:, 0], atol=1e-12)
+
+
+def test_served_job_returns_string_values(tnlib):
+    """A job's Pauli strings (tn_job.ops) come back with its <Z_v>: the same
+    values, by both methods, as tn_expect on a handle evolved alone (the
+    paper's printed weight-10 string on 127 qubits and a weight-17 string)."""
+    from oracle import clifford as OC
+    n, edges, cols = tnlib.heavy_hex(7, 15)
+    from oracle import graph as OG
+    g = OG.eagle127()
+    s10 = dict(OC.string_from_z(g, 13, 5).ops)
+    s17 = dict(OC.string_from_z(g, 9, 5).ops)
+    strings = [(s10, 1), (s17, -1)]   # both of the form U^n' Z_i U^-n' (method 1 needs that)
+    chi, theta, steps = 8, 0.6, 5
+    with tnlib.TNState(n, edges, cols, chi=chi) as s:
+        s.apply_floquet(theta, steps)
+        want = {m: s.expect(strings, method=m) for m in (0, 1)}
+    with tnlib.Server(slots=2) as srv:
+        t = {m: srv.submit(n, edges, cols, chi, theta, steps, ops=strings, method=m) for m in (0, 1)}
+        for m in (0, 1):
+            z, info = srv.wait(t[m])
+            assert info["ops"].shape == (2,)
+            assert np.abs(info["ops"] - want[m]).max() < 1e-12

@@ -439,3 +439,58 @@ def test_bp_error_of_a_uniform_ring_is_the_transfer_matrix_closed_form():
         want = want / want[0]
         assert np.allclose(s / s[0], want, atol=1e-9)
         assert abs(err - (1 - np.sqrt(1 / np.sum(want ** 2)))) < 1e-9
+
+
+def _cut_schmidt(psi, n, left):
+    """Schmidt values and vectors of psi across the cut (left, rest); qubit q is
+    bit q of the amplitude index."""
+    right = [q for q in range(n) if q not in left]
+    t = psi.reshape([2] * n)                      # axis i <-> qubit n-1-i
+    axes = [n - 1 - q for q in left] + [n - 1 - q for q in right]
+    m = np.transpose(t, axes).reshape(2 ** len(left), -1)
+    u, s, vh = np.linalg.svd(m, full_matrices=False)
+    return u, s, vh, axes
+
+
+def _truncate_cut(psi, n, left, chi):
+    """The best rank-chi approximation of psi across the cut, normalised."""
+    u, s, vh, axes = _cut_schmidt(psi, n, left)
+    m = (u[:, :chi] * s[:chi]) @ vh[:chi] / np.linalg.norm(s[:chi])
+    t = m.reshape([2] * n)
+    inv = np.argsort(axes)
+    return np.transpose(t, inv).reshape(-1), s
+
+
+@pytest.mark.parametrize("case", ["path8", "star7"])
+def test_truncated_simple_update_is_the_optimal_schmidt_truncation(case):
+    """Pin of the oracle's truncation branch (Methods, "The Vidal gauge" and "The
+    simple update procedure").  On a tree the converged BP messages are the exact
+    environments of each bond, so one simple update of exp(+i pi/4 Z_v Z_w) with a
+    bond dimension below the edge's Schmidt rank must keep exactly the chi
+    largest Schmidt values of the gated statevector across that edge, normalised,
+    and the state it leaves must be the statevector's best rank-chi truncation
+    across the cut: <Z_q> of every qubit agrees after BP regauges the tree."""
+    if case == "path8":
+        g = G.path(8)
+        e, left = 3, [0, 1, 2, 3]                 # edge (3, 4)
+    else:
+        g = G.star3_tree()
+        e, left = 0, [1, 2]                       # edge (0, 1): the arm {1, 2} against the rest
+    theta, steps, chi_t = 0.7, 3, 3
+    st = B.run(g, 64, theta, steps)              # exact: every bond below 2^steps <= 64
+    psi = S.evolve(g, theta, steps)
+    v, w = g.edges[e]
+    s_v = 1 - 2 * ((np.arange(2 ** g.n) >> v) & 1)
+    s_w = 1 - 2 * ((np.arange(2 ** g.n) >> w) & 1)
+    psi_g = psi * np.exp(1j * np.pi / 4 * s_v * s_w)
+    psi_t, s_full = _truncate_cut(psi_g, g.n, left, chi_t)
+    assert np.count_nonzero(s_full > 1e-12 * s_full[0]) > chi_t       # the gate truncates
+    assert (s_full[chi_t - 1] - s_full[chi_t]) / s_full[0] > 1e-3      # unique kept subspace
+    st.chi = chi_t
+    st.apply_zz(e, +1)
+    kept = np.real(np.diag(st.M[(v, e)]))
+    want = s_full[:chi_t] / np.linalg.norm(s_full[:chi_t])
+    assert np.allclose(kept, want, atol=1e-10)
+    assert abs(st.discarded[-1] - np.sum(s_full[chi_t:] ** 2) / np.sum(s_full ** 2)) < 1e-10
+    st.bp_converge(1e-12, 1000)
+    assert np.abs(st.all_z() - S.z_expectations(psi_t, g.n)).max() < 1e-10
