@@ -315,10 +315,13 @@ tn_status tn_truncation_solve_ex(const float* gram, float* dmat, double* s_out, 
  * edges at chi = 64, 42 at chi = 32); larger requests fail with TN_EINVAL and a
  * message giving the limit.  No cudaMalloc, cudaFree or other allocating call
  * is made.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  Every call shares the one array, which keeps the last
- * call's contents: calls that overlap on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life of
+ * the process; a cudaDeviceReset in the application destroys the context that
+ * address belongs to, so do not call this function on that device afterwards.
+ * Like tn_truncation_solve it returns only after its stream has finished the
+ * work (it reads the error flag back).  Every call shares the one array, which
+ * keeps the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller.
  */
 tn_status tn_truncation_solve_noalloc(const float* gram, float* dmat, double* s_out,
                                       int32_t n_edges, int32_t chi, int32_t sign,

@@ -288,7 +288,11 @@ extern "C" tn_status tn_bp_error(tn_handle* h, int32_t e, double* error, double*
   if (E.lab[0] != m) E = permute(E, {1, 0});
   const int64_t ru = E.dim[0], rw = E.dim[1];
   // the host Jacobi on E^H E is cubic in its size: chi up to 32 on the cut edge
-  if (rw > 1024) { tnbp::set_error("edge environment above 1024 x 1024"); return TN_EINVAL; }
+  if (rw > 1024) {
+    tnbp::set_error("edge environment with more than 1024 columns (the cut bond's index on the "
+                    "edge's second endpoint, ket x bra)");
+    return TN_EINVAL;
+  }
   std::vector<cplx> hm((size_t)rw * rw, cplx(0.0, 0.0));  // E^H E
   for (int64_t i = 0; i < rw; ++i)
     for (int64_t j = i; j < rw; ++j) {

@@ -26,7 +26,9 @@ double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_solve_scratch on the current device.  In host code the
 // array's name is only a host-side stand-in, so the address is looked up once
-// per device with that device current and cached.
+// per device with that device current and cached for the life of the process
+// (a cudaDeviceReset by the application would leave the cached address
+// pointing into a destroyed context; the header says so).
 tn_status scratch_address(double** out) {
   int dev = 0;
   TN_CUDA_TRY(cudaGetDevice(&dev));

@@ -72,3 +72,22 @@ def test_noalloc_rejects_requests_beyond_its_workspace(tnlib):
     assert st == -1
     msg = L.tn_last_error().decode()
     assert "16777216" in msg and "workspace" in msg
+
+
+def test_noalloc_recovers_after_a_failed_call(tnlib):
+    """The workspace keeps the previous call's contents, error flag included: a
+    call whose spectrum is zero (an all-zero Gram) fails with TN_ENUMERIC, and
+    the next, valid call on the same array must succeed and match the
+    allocating solve."""
+    import torch
+    L = tnlib.lib()
+    n_edges, chi = 4, 8
+    zero = torch.zeros(n_edges * 8 * chi * chi, device="cuda")
+    st, _, _ = call(L.tn_truncation_solve_noalloc, zero, chi, n_edges, 1)
+    assert st == -4   # TN_ENUMERIC
+    g = torch.from_numpy(random_grams(n_edges, chi, 12, 23).reshape(-1)).cuda()
+    st_a, d_a, s_a = call(L.tn_truncation_solve, g, chi, n_edges, 1)
+    st_b, d_b, s_b = call(L.tn_truncation_solve_noalloc, g, chi, n_edges, 1)
+    assert st_a == 0 and st_b == 0, L.tn_last_error().decode()
+    np.testing.assert_allclose(s_b, s_a, atol=TOL, rtol=0)
+    np.testing.assert_allclose(d_b, d_a, atol=TOL * max(1.0, np.abs(d_a).max()), rtol=0)
