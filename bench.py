@@ -73,6 +73,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--serve-jobs", type=int, default=16,
                    help="jobs of the serving leg (0: skip)")
+    p.add_argument("--config4", action="store_true",
+                   help="also run the large-chi periodic-cell leg (chi 128 and 256, 50 steps, "
+                        "theta 0.4 / 0.7 / 1.0, BF16X3 against FP32) and print its own line")
+    p.add_argument("--config4-steps", type=int, default=50)
     return p.parse_args()
 
 
@@ -165,6 +169,53 @@ def serve_leg(tn, args):
             "sample": "first %d jobs of the seeded stream with <= 127 qubits and chi <= 64 "
                       "(27- and 127-qubit graphs, chi 16/32/64, 5-20 steps), prec %s"
                       % (len(lat), args.prec)}
+
+
+def config4_leg(tn, args):
+    """The large-chi leg (the infinite heavy-hex lattice through its periodic
+    5-site cell, reading r14): for chi in {128, 256} and theta_h in {0.4, 0.7,
+    1.0}, `steps` Floquet steps with split-BF16 contractions and with the plain
+    FP32 path, both with the refined FP64 truncation solve; per run the steps/s,
+    the largest |<Z>| difference between the two precisions, and the mean over
+    the cell's six bonds of the entanglement entropy s = -sum l^2 log2 l^2
+    (reading r16)."""
+    import torch
+    # the 5-site cell: corners A = 0, B = 1, bond midpoints 2, 3, 4; A-m_k has
+    # colour k - 1 and B-m_k colour k mod 3
+    cell_edges = np.array([(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (1, 4)], dtype=np.int32)
+    cell_cols = np.array([0, 1, 2, 1, 2, 0], dtype=np.uint8)
+
+    class _Cell:
+        n, edges, colours = 5, cell_edges, cell_cols
+    g = _Cell()
+    rows = []
+    for chi in (128, 256):
+        for theta in (0.4, 0.7, 1.0):
+            res = {}
+            for prec in ("bf16x3", "fp32"):
+                stream = torch.cuda.Stream()
+                with tn.TNState(g.n, g.edges, g.colours, chi=chi, prec=prec, stream=stream) as s:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s.apply_floquet(theta, args.config4_steps)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    res[prec] = {"z": s.expect_z_all(),
+                                 "s": float(np.mean([s.entanglement_entropy(e)
+                                                     for e in range(len(g.edges))])),
+                                 "steps_per_s": args.config4_steps / (ms * 1e-3)}
+            rows.append({"chi": chi, "theta_h": theta, "steps": args.config4_steps,
+                         "bf16x3_steps_per_s": round(res["bf16x3"]["steps_per_s"], 3),
+                         "fp32_steps_per_s": round(res["fp32"]["steps_per_s"], 3),
+                         "max_dz_bf16x3_vs_fp32": float(np.abs(res["bf16x3"]["z"] -
+                                                               res["fp32"]["z"]).max()),
+                         "entropy_bf16x3": round(res["bf16x3"]["s"], 6),
+                         "entropy_fp32": round(res["fp32"]["s"], 6),
+                         "z_mean_fp32": float(np.mean(res["fp32"]["z"]))})
+    return {"leg": "config4: periodic 5-site cell (infinite heavy-hex lattice), refined FP64 "
+                   "truncation solve", "runs": rows}
 
 
 def eagle():
@@ -547,6 +598,8 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if args.config4 and rank == 0:
+        print(json.dumps(config4_leg(tn, args)), flush=True)
 
 
 # ---------------------------------------------------------------- reference

@@ -78,7 +78,12 @@ __host__ __device__ __forceinline__ int64_t row_off3(int m, int M2, int M3, int6
 
 // Launch helpers implemented in kernels.cu / solve.cu.  All return a
 // cudaError_t from the launch.
-cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s);
+// CUDA-core complex GEMM (kernels.cu); with part != nullptr (part_cap floats) a
+// launch whose grid is under one wave is split over K into partials (cgemm_plan
+// gives the count and the partial floats) and summed by the fixed-order reduce.
+int cgemm_plan(const GemmDesc& d, size_t* part_floats);
+cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s, float* part = nullptr,
+                         size_t part_cap = 0, int* n_kernels = nullptr);
 // Tensor-core version (tc_gemm.cu) for TN_TF32 / TN_BF16 descriptors.  part:
 // scratch for K-split partial products (tc_plan gives the size); err: bit 1 is
 // set when a device-side wait gave up.
@@ -210,6 +215,7 @@ struct RefineLayout {
   int64_t lam1;   // [chi]: refined eigenvalues of the kept columns
   int64_t misc;   // [4]: sum of all sigma^2 of the start, FP32 sweeps
   int64_t ints;   // int32 [2 chi] perm, [2] rank, [1] active columns
+  int64_t S;      // [n][n] float2: FP32 G_w and its Cholesky factor (2 chi > 128 only)
   int64_t stride;
 };
 __host__ __device__ inline RefineLayout refine_layout(int chi) {
@@ -223,6 +229,7 @@ __host__ __device__ inline RefineLayout refine_layout(int chi) {
   l.lam1 = l.lam0 + n;
   l.misc = l.lam1 + chi;
   l.ints = l.misc + 4;
+  l.S = l.ints + chi + 4;  // after the 2 chi + 3 ints
   l.stride = 12 * n * n;  // solve_work_doubles(chi)
   return l;
 }
@@ -231,6 +238,9 @@ size_t solve_work_doubles(int chi);
 // Shared-memory solve with FP32 rotations (solve32.cu), chi <= 64.
 bool solve32_supported(int chi);
 cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t s);
+// The refined solve's FP32 starting basis for 2 chi > 128 (solve32.cu): the
+// bond matrix in the global workspace, one CTA per edge, 16 <= chi <= 256.
+cudaError_t launch_basis_gmem(const SolveArgs& a, cudaStream_t s);
 // Refined solve (solve_refine.cu): FP64 Cholesky, FP32 starting basis, FP64
 // Newton refinement and FP64 leg matrices; chi <= 64.  work: solve_work_doubles
 // per edge.

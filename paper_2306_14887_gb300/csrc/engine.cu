@@ -476,7 +476,8 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls, size_t begin = 0,
     } else if (use_tensor_cores(h) && !tiny) {
       TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, stream, &nk));
     } else {
-      TN_CUDA_TRY(launch_cgemm(L.d, stream));
+      // a tiny-grid launch on the main stream may split K into the partial buffer
+      TN_CUDA_TRY(launch_cgemm(L.d, stream, on_side ? nullptr : h->part, h->part_floats, &nk));
     }
     if (pi >= 0) {
       double f, b;
@@ -504,6 +505,9 @@ bool side_safe(const tn_handle* h, const Plan& P, size_t begin) {
       size_t pf = 0;
       tc_plan(L.d, &q, &sp, &pf);
       if (sp > 1) return false;
+    } else {
+      size_t pf = 0;
+      if (cgemm_plan(L.d, &pf) > 1) return false;
     }
   }
   return true;
@@ -1496,20 +1500,24 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   h->copyback.resize(nl);
   for (int li = 0; li < nl; ++li) build_gate_plans(h, li);
   build_rho_plan(h);
-  if (use_tensor_cores(h)) {
+  {
     size_t need = 0;
     std::vector<Plan*> plans = {&h->sweep, &h->rho_prep};
     for (auto& p : h->gate_env) plans.push_back(&p);
     for (auto& p : h->rebuild) plans.push_back(&p);
     for (Plan* p : plans)
       for (auto& L : p->L) {
-        int q, sp;
         size_t pf = 0;
-        tc_plan(L.d, &q, &sp, &pf);
+        if (use_tensor_cores(h)) {
+          int q, sp;
+          tc_plan(L.d, &q, &sp, &pf);
+          need = std::max(need, pf);
+        }
+        cgemm_plan(L.d, &pf);  // the CUDA-core launches of every precision
         need = std::max(need, pf);
       }
     // the TMA closes take at most 2 x 152 CTAs of partials over the entries
-    need = std::max<size_t>(need, (size_t)2 * 2 * 152 * 2 * 4096);
+    if (use_tensor_cores(h)) need = std::max<size_t>(need, (size_t)2 * 2 * 152 * 2 * 4096);
     h->part_floats = std::max<size_t>(need, 16);
     h->part = (float*)dev_alloc(h, sizeof(float) * h->part_floats);
     if (!h->part) { delete[] h->h_stats; set_error("device allocation failed"); return fail(TN_ENOMEM); }

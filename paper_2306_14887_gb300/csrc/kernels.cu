@@ -41,10 +41,13 @@ __device__ __forceinline__ int64_t koff(int k, int K2, int64_t s1, int64_t s2) {
   return (int64_t)k1 * s1 + (int64_t)k2 * s2;
 }
 
-__global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
+__global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d, float* part, int splits,
+                                                          int k_per_split) {
   __shared__ float As[2][BK][BM + 1];
   __shared__ float Bs[2][BK][BN + 1];
-  const int z = blockIdx.z;
+  int z = blockIdx.z;
+  const int split = z % splits;
+  z /= splits;
   const int outer = z / d.n_inner;
   const int inner = z - outer * d.n_inner;
   const float* A = d.A[outer] + inner * d.a_in;
@@ -53,7 +56,10 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int K = d.K1 * d.K2;
+  const int Kall = d.K1 * d.K2;
+  // this CTA's K range (all of K without split-K)
+  const int kb = split * k_per_split;
+  const int K = min(Kall, kb + k_per_split);
   const bool a_kfast = (d.a_k2 == 1) && !(d.M2 > 1 && d.M3 <= 1 && d.a_m2 == 1) &&
                        !(d.M3 > 1 && d.a_m3 == 1);
   const bool b_nfast = (d.b_n == 1);
@@ -66,7 +72,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = cmpr[i][j] = cmpi[i][j] = 0.f;
 
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  for (int k0 = kb; k0 < K; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int idx = tid + r * 256;
@@ -149,6 +155,14 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= d.N) continue;
+      if (splits > 1) {
+        // split-K partial [split][outer][inner][re|im][M][N], summed by the reduce
+        float* q = part + ((((int64_t)split * d.n_outer + outer) * d.n_inner + inner) * 2) *
+                              (int64_t)d.M * d.N;
+        q[(int64_t)m * d.N + n] = accr[i][j];
+        q[(int64_t)d.M * d.N + (int64_t)m * d.N + n] = acci[i][j];
+        continue;
+      }
       const int64_t off = ROW_C(d, m) + (int64_t)n * d.c_n;
       if (d.accumulate) {
         C[off] += accr[i][j];
@@ -162,11 +176,35 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d) {
 }
 }  // namespace
 
-cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s) {
+// Split-K for the CUDA-core GEMM: a launch whose grid is under one wave (152
+// CTAs: a few sites with a long contraction, e.g. the closes) is split into at
+// most 64 pieces of at least 256 K values, each summed with the compensated
+// slices, the pieces then summed in FP64 in a fixed order by the reduce.
+int cgemm_plan(const GemmDesc& d, size_t* part_floats) {
+  const int64_t K = (int64_t)d.K1 * d.K2;
+  const int64_t ctas = (int64_t)((d.N + BN - 1) / BN) * ((d.M + BM - 1) / BM) * d.n_outer * d.n_inner;
+  int s = 1;
+  if (ctas < 152)
+    while (s < 64 && ctas * s * 2 <= 2 * 152 && K / (2 * s) >= 256) s *= 2;
+  *part_floats = s > 1 ? (size_t)s * d.n_outer * d.n_inner * 2 * d.M * d.N : 0;
+  return s;
+}
+
+cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s, float* part, size_t part_cap,
+                         int* n_kernels) {
+  if (n_kernels) *n_kernels = 0;
   if (d.M <= 0 || d.N <= 0 || d.n_outer <= 0 || d.n_inner <= 0) return cudaSuccess;
-  dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, d.n_outer * d.n_inner);
-  cgemm_simt_kernel<<<grid, 256, 0, s>>>(d);
-  return cudaGetLastError();
+  size_t pf = 0;
+  int splits = part ? cgemm_plan(d, &pf) : 1;
+  if (splits > 1 && pf > part_cap) splits = 1;  // the caller's partial buffer is too small
+  const int K = d.K1 * d.K2;
+  const int kps = splits > 1 ? ((K + splits - 1) / splits + BK - 1) / BK * BK : K;
+  dim3 grid((d.N + BN - 1) / BN, (d.M + BM - 1) / BM, d.n_outer * d.n_inner * splits);
+  cgemm_simt_kernel<<<grid, 256, 0, s>>>(d, part, splits, kps);
+  if (n_kernels) *n_kernels = splits > 1 ? 2 : 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  return launch_tc_reduce(d, part, splits, s);
 }
 
 // ---------------------------------------------------------------------------

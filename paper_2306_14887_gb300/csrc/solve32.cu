@@ -221,6 +221,7 @@ __device__ Smem carve(unsigned char* base, int chi) {
 __device__ __noinline__ void write_basis(const SolveArgs& a, const Smem& s, float2* X, int edge,
                                          int chi, int sweeps) {
   const int n = 2 * chi, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = (int)(blockDim.x >> 5);
   const RefineLayout lay = refine_layout(chi);
   double* rbase = a.work + (int64_t)edge * lay.stride;
   int* rints = reinterpret_cast<int*>(rbase + lay.ints);
@@ -278,7 +279,7 @@ __device__ __noinline__ void write_basis(const SolveArgs& a, const Smem& s, floa
           __syncthreads();
         }
         // x_m -= <u_k, x_m> u_k for the tail rows after k
-        for (int m = max(k + 1, head) + warp; m < act; m += kWarps) {
+        for (int m = max(k + 1, head) + warp; m < act; m += nwarps) {
           const int rm = s.order[m];
           float gr = 0.f, gi = 0.f;
           for (int c = lane; c < n; c += 32) {
@@ -882,6 +883,184 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   }
 }
 
+// ----------------------------------------------------------------------
+// The FP32 starting basis of the refined solve for 2 chi > 128, where the
+// bond matrix no longer fits in shared memory: the same steps as basis mode of
+// solve32_kernel, with G_w, its Cholesky factor and K^T in the edge's global
+// workspace (L2-resident) and a round-robin pair order.  One CTA of
+// kGThreads threads per edge.
+constexpr int kGThreads = 512;
+constexpr int kGMaxN = 512;           // 2 chi <= 512 (chi <= 256)
+constexpr int kGVals = kGMaxN / 32;   // row values per lane
+
+__global__ void __launch_bounds__(kGThreads, 1) basis_gmem_kernel(SolveArgs a) {
+  __shared__ double sig[kGMaxN];
+  __shared__ int order[kGMaxN], perm_w[kGMaxN], src[kGMaxN];
+  __shared__ float2 colk[kGMaxN];
+  __shared__ int counter[4], red_i[4], rank_s[4];
+  __shared__ float red_v[4], dmax0[4];
+  __shared__ double red_d[kGThreads / 32];
+  const int chi = a.chi, n = 2 * chi, half = n / 2;
+  const int64_t c2 = (int64_t)chi * chi;
+  const int edge = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kGThreads / 32;
+  const RefineLayout lay = refine_layout(chi);
+  double* rbase = a.work + (int64_t)edge * lay.stride;
+  const int* rints = reinterpret_cast<const int*>(rbase + lay.ints);
+  const double2* L64 = reinterpret_cast<const double2*>(rbase + lay.L);
+  float2* Gw = reinterpret_cast<float2*>(rbase + lay.S);   // n x n: G_w, then L_w
+  float2* X = reinterpret_cast<float2*>(rbase + lay.U1);   // n x n: K^T, then its rotations
+  const float* gw = a.gram + (int64_t)edge * 8 * c2 + 4 * c2;
+  const float sg = (float)a.sign;
+  // 1. G_w from conj(N_q^w) with the phases of the gate split (as solve32_kernel)
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    const int ki = i / chi, ei = i % chi, kj = j / chi, ej = j % chi;
+    const int64_t o = (int64_t)ei * chi + ej;
+    const float2 g0 = make_float2(gw[o], -gw[c2 + o]);
+    const float2 g1 = make_float2(gw[2 * c2 + o], -gw[3 * c2 + o]);
+    float2 v;
+    if (ki == kj) {
+      v = make_float2(g0.x + g1.x, g0.y + g1.y);
+    } else {
+      const float2 d = make_float2(g0.x - g1.x, g0.y - g1.y);
+      const float f = (ki == 0) ? -sg : sg;
+      v = make_float2(-f * d.y, f * d.x);
+    }
+    Gw[idx] = v;
+  }
+  __syncthreads();
+  // 2. FP32 pivoted Cholesky of G_w in place (global memory)
+  const Group gall{0, kGThreads, 0};
+  pivoted_cholesky32(Gw, n, n, perm_w, 1e-7f, &rank_s[2], red_i, red_v, dmax0, colk, gall);
+  // 3. K^T[j][(b, i)] = sum_{t' >= i} conj(L_w[src(b, t')][j]) conj(L_b[t'][i]) with
+  //    src(b, t') = pinv_w(b chi + perm_b[t']) (as solve32_kernel, R_w = L_w^H P_w^T)
+  for (int t = tid; t < n; t += blockDim.x) order[perm_w[t]] = t;  // pinv_w
+  __syncthreads();
+  for (int bt = tid; bt < n; bt += blockDim.x) {
+    const int b = bt / chi, tp = bt % chi;
+    src[bt] = order[b * chi + rints[b * chi + tp]];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const int o = idx / n, j = idx % n;   // output column (b, i) = o, row j: consecutive j per warp
+    const int b = o / chi, i = o % chi;
+    const double2* Lb = L64 + b * c2;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int tp = i; tp < chi; ++tp) {
+      const double2 l = Lb[(int64_t)tp * chi + i];
+      const float2 w = Gw[(int64_t)src[b * chi + tp] * n + j];
+      // conj(w) conj(l) = conj(w l)
+      const float lx = (float)l.x, ly = (float)l.y;
+      acc.x += w.x * lx - w.y * ly;
+      acc.y -= w.x * ly + w.y * lx;
+    }
+    X[(int64_t)j * n + o] = acc;
+  }
+  __syncthreads();
+  // 4. One-sided Jacobi on the rows of X (columns of K), round-robin pairs;
+  //    pairs orthogonal to orth_tol, or with an overlap below 1e-12 ||K||_F^2,
+  //    are left alone; a sweep that rotates nothing ends the iteration
+  {
+    double acc = 0.0;
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const float2 v = X[idx];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) red_d[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps; ++w) t += red_d[w];
+      sig[0] = t;
+    }
+    __syncthreads();
+  }
+  const float abs_floor = (float)(kAbsTol * sig[0]);
+  const float orth_tol = a.orth_tol > 0.f ? a.orth_tol : 2e-6f;
+  const int npl = n / 32;  // n is a multiple of 32 here
+  int sweeps = 0;
+  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    ++sweeps;
+    if (tid == 0) counter[0] = 0;
+    __syncthreads();
+    for (int r = 0; r < n - 1; ++r) {
+      for (int k = warp; k < half; k += nwarps) {
+        int p, q;
+        if (k == 0) { p = r; q = n - 1; }
+        else { p = (r + k) % (n - 1); q = (r - k + (n - 1)) % (n - 1); }
+        float2 xp[kGVals], xq[kGVals];
+        float al = 0.f, be = 0.f, gr = 0.f, gi = 0.f;
+#pragma unroll
+        for (int u = 0; u < kGVals; ++u) {
+          if (u < npl) {
+            const int c = u * 32 + lane;
+            xp[u] = X[(int64_t)p * n + c];
+            xq[u] = X[(int64_t)q * n + c];
+            al += xp[u].x * xp[u].x + xp[u].y * xp[u].y;
+            be += xq[u].x * xq[u].x + xq[u].y * xq[u].y;
+            gr += xp[u].x * xq[u].x + xp[u].y * xq[u].y;
+            gi += xp[u].x * xq[u].y - xp[u].y * xq[u].x;
+          }
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        gr = warp_sum(gr);
+        gi = warp_sum(gi);
+        const float gm = sqrtf(gr * gr + gi * gi);
+        if (gm > orth_tol * sqrtf(al * be) && gm > abs_floor && gm > 0.f) {
+          const float2 ph = make_float2(gr / gm, -gi / gm);  // e^{-i phi}
+          const float tau = (be - al) / (2.f * gm);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          const float cs = 1.f / sqrtf(1.f + t * t);
+          const float sn = t * cs;
+#pragma unroll
+          for (int u = 0; u < kGVals; ++u) {
+            if (u < npl) {
+              const int c = u * 32 + lane;
+              const float2 pq = cmulf(ph, xq[u]);
+              X[(int64_t)p * n + c] = make_float2(cs * xp[u].x - sn * pq.x, cs * xp[u].y - sn * pq.y);
+              X[(int64_t)q * n + c] = make_float2(sn * xp[u].x + cs * pq.x, sn * xp[u].y + cs * pq.y);
+            }
+          }
+          if (lane == 0) atomicAdd(&counter[0], 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = counter[0];
+    __syncthreads();
+    if (rotated == 0) break;
+  }
+  // 5. sigma_j = ||row j|| (FP64), decreasing order, then the basis
+  for (int j = warp; j < n; j += nwarps) {
+    double acc = 0.0;
+    for (int c = lane; c < n; c += 32) {
+      const float2 v = X[(int64_t)j * n + c];
+      acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) sig[j] = sqrt(acc);
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double si = sig[i];
+    int rk = 0;
+    for (int j = 0; j < n; ++j) {
+      const double sj = sig[j];
+      rk += (sj > si) || (sj == si && j < i);
+    }
+    order[rk] = i;
+  }
+  __syncthreads();
+  Smem sm{};
+  sm.sig = sig;
+  sm.order = order;
+  sm.counter = counter;
+  write_basis(a, sm, X, edge, chi, sweeps);
+}
+
 size_t smem_bytes(int chi) {
   const int n = 2 * chi;
   return sizeof(float2) * (size_t)n * n + sizeof(float2) * 2 * chi * (chi + 1) +
@@ -893,6 +1072,13 @@ size_t smem_bytes(int chi) {
 }  // namespace
 
 bool solve32_supported(int chi) { return chi >= 1 && chi <= kMaxChi; }
+
+cudaError_t launch_basis_gmem(const SolveArgs& a, cudaStream_t st) {
+  if (a.n_edges <= 0) return cudaSuccess;
+  if (a.chi < 16 || 2 * a.chi > kGMaxN || (2 * a.chi) % 32 != 0) return cudaErrorInvalidValue;
+  basis_gmem_kernel<<<a.n_edges, kGThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t st) {
   if (a.n_edges <= 0) return cudaSuccess;

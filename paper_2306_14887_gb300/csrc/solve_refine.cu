@@ -82,7 +82,9 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kJG = 8;              // output columns accumulated together per warp row
 constexpr int kJU = 4;              // output columns per thread in the basis update
-constexpr int kMaxChi = 64;         // the FP32 phase holds 2 chi <= 128 in shared memory
+constexpr int kSmemChi = 64;   // up to here the FP32 basis and the FP64 Cholesky run in
+                               // shared memory; above, in the edge's global workspace
+constexpr int kMaxChi = 256;
 constexpr int kSmemBudget = 200 * 1024;
 // Head columns, sigma >= 1e-3 sigma_1: the FP32 start is accurate enough there
 // for one Newton step to reach FP64 accuracy.  Below, the start is limited by
@@ -193,15 +195,20 @@ __device__ void pivoted_cholesky64(cd* A, int m, int ld, int* perm, double rel_t
 // Block b = blockIdx.x of edge blockIdx.y: G_b = conj(N_b^v) -> L_b, perm_b, rank_b.
 __global__ void __launch_bounds__(kThreads) chol64_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* A = reinterpret_cast<cd*>(smem_raw);
   __shared__ int piv_s, rank_s;
   __shared__ double pv_s, d0_s;
-  const int b = blockIdx.x, edge = blockIdx.y, chi = a.chi, ld = chi + 1;
+  const int b = blockIdx.x, edge = blockIdx.y, chi = a.chi;
   const int64_t c2 = (int64_t)chi * chi;
   const float* g = a.gram + (int64_t)edge * 8 * c2 + (int64_t)b * 2 * c2;
   const RefineLayout lay = refine_layout(chi);
   double* base = a.work + (int64_t)edge * lay.stride;
   int* ints = reinterpret_cast<int*>(base + lay.ints);
+  // the factorisation runs in shared memory (padded rows) up to kSmemChi and in
+  // place in the edge's L block of the workspace above
+  const bool in_smem = chi <= kSmemChi;
+  const int ld = in_smem ? chi + 1 : chi;
+  cd* A = in_smem ? reinterpret_cast<cd*>(smem_raw)
+                  : reinterpret_cast<cd*>(base + lay.L) + (int64_t)b * c2;
   for (int idx = threadIdx.x; idx < chi * chi; idx += blockDim.x) {
     const int i = idx / chi, j = idx - i * chi;
     A[i * ld + j] = {(double)g[idx], -(double)g[c2 + idx]};
@@ -209,10 +216,11 @@ __global__ void __launch_bounds__(kThreads) chol64_kernel(SolveArgs a) {
   __syncthreads();
   pivoted_cholesky64(A, chi, ld, ints + b * chi, a.gram_cut, &rank_s, &piv_s, &pv_s, &d0_s);
   cd* L = reinterpret_cast<cd*>(base + lay.L) + (int64_t)b * c2;
-  for (int idx = threadIdx.x; idx < chi * chi; idx += blockDim.x) {
-    const int i = idx / chi, j = idx - i * chi;
-    L[idx] = A[i * ld + j];
-  }
+  if (in_smem)
+    for (int idx = threadIdx.x; idx < chi * chi; idx += blockDim.x) {
+      const int i = idx / chi, j = idx - i * chi;
+      L[idx] = A[i * ld + j];
+    }
   if (threadIdx.x == 0) ints[2 * chi + b] = rank_s;
   // rows (k = b, e) of conj(G_w) in FP64 (exact from the FP32 inputs):
   // conj(G_w)[(k,e), (k',e')] = N_0 + N_1 for k = k', +s i (N_0 - N_1) for
@@ -692,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1) legs_kernel(SolveArgs a, int cwma
 // Shared-memory limits of the refined solve's kernels, raised once to the
 // largest request any chi <= kMaxChi makes, so that concurrent launches (the
 // job server's slots) never lower a limit another thread relies on.
-constexpr size_t kCholSmemMax = sizeof(cd) * kMaxChi * (kMaxChi + 1);
+constexpr size_t kCholSmemMax = sizeof(cd) * kSmemChi * (kSmemChi + 1);
 constexpr size_t kRefineSmemMax = kSmemBudget + 4096;
 constexpr size_t kLegsSmemMax = kSmemBudget / 2 + 8192;
 
@@ -721,14 +729,17 @@ int sm_count() {
 
 }  // namespace
 
-bool solve_refined_supported(int chi) { return chi >= 1 && chi <= kMaxChi && solve32_supported(chi); }
+bool solve_refined_supported(int chi) {
+  if (chi >= 1 && chi <= kSmemChi) return solve32_supported(chi);
+  return chi <= kMaxChi && (2 * chi) % 32 == 0;  // the global-memory basis kernel
+}
 
 cudaError_t launch_solve_refined_basis(const SolveArgs& a, cudaStream_t st) {
   if (a.n_edges <= 0) return cudaSuccess;
   if (!solve_refined_supported(a.chi)) return cudaErrorInvalidValue;
   const int chi = a.chi;
   // 1. FP64 Cholesky of the v-side Gram blocks, conj(G_w) in FP64
-  const size_t sm_chol = sizeof(cd) * (size_t)chi * (chi + 1);
+  const size_t sm_chol = chi <= kSmemChi ? sizeof(cd) * (size_t)chi * (chi + 1) : 0;
   cudaError_t e = refine_prepare();
   if (e != cudaSuccess) return e;
   chol64_kernel<<<dim3(2, a.n_edges), kThreads, sm_chol, st>>>(a);
@@ -736,7 +747,7 @@ cudaError_t launch_solve_refined_basis(const SolveArgs& a, cudaStream_t st) {
   // 2. FP32 starting basis
   SolveArgs b = a;
   b.basis = 1;
-  return launch_solve32(b, st);
+  return chi <= kSmemChi ? launch_solve32(b, st) : launch_basis_gmem(b, st);
 }
 
 cudaError_t launch_solve_refined_newton(const SolveArgs& a, cudaStream_t st) {

@@ -67,7 +67,7 @@ struct TcArgs {
   int x3;          // split precision: x = hi + lo, D += A_hi B_hi + A_hi B_lo + A_lo B_hi
   int mr, nr, kr;  // real GEMM sizes
   int tn;          // N tile (multiple of 16, <= 128)
-  int splits;      // K splits (QUAD only)
+  int splits;      // K splits
   int k_per_split; // real K per split (multiple of the K tile)
   float* part;     // partial outputs [split][outer][inner][2][M][N] (splits > 1)
   int* err;
@@ -489,7 +489,24 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
     const int row = warp * 32 + lane;  // accumulator row = TMEM lane
     const int mr = m0 + row;
     float* C = d.C[outer] + inner * d.c_in;
-    if (!t.quad) {
+    if (!t.quad && t.splits > 1) {
+      // split-K partial [split][outer][inner][re|im][M][N] (an empty split writes zeros)
+      float* q = t.part + ((((int64_t)split * d.n_outer + outer) * d.n_inner + inner) * 2) *
+                              (int64_t)d.M * d.N;
+      for (int c0 = 0; c0 < t.tn; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
+        if (mr >= t.mr) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int nr = n0 + c0 + j;
+          if (nr >= t.nr) break;
+          const int tt = nr >= d.N;
+          const int n = nr - tt * d.N;
+          q[(int64_t)tt * d.M * d.N + (int64_t)mr * d.N + n] = (ok && ntiles > 0) ? v[j] : 0.f;
+        }
+      }
+    } else if (!t.quad) {
       for (int c0 = 0; c0 < t.tn; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, v);
@@ -570,16 +587,17 @@ __global__ void tc_reduce_kernel(GemmDesc d, const float* part, int splits) {
   float* C = d.C[outer] + inner * d.c_in;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < M * N; idx += gridDim.x * blockDim.x) {
     const int m = idx / N, n = idx - m * N;
-    float cr = 0.f, ci = 0.f;
+    // partials summed in FP64 in split order, rounded once
+    double cr = 0.0, ci = 0.0;
     for (int s = 0; s < splits; ++s) {
       const float* q =
           part + ((((int64_t)s * d.n_outer + outer) * d.n_inner + inner) * 2) * (int64_t)M * N;
-      cr += q[idx];
-      ci += q[(int64_t)M * N + idx];
+      cr += (double)q[idx];
+      ci += (double)q[(int64_t)M * N + idx];
     }
     float* p = C + ROW_C(d, m) + (int64_t)n * d.c_n;
-    if (d.accumulate) { p[0] += cr; p[d.plane_c] += ci; }
-    else { p[0] = cr; p[d.plane_c] = ci; }
+    if (d.accumulate) { p[0] = (float)((double)p[0] + cr); p[d.plane_c] = (float)((double)p[d.plane_c] + ci); }
+    else { p[0] = (float)cr; p[d.plane_c] = (float)ci; }
   }
 }
 
@@ -601,15 +619,27 @@ bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {
   *quad = (2 * d.M <= kTM && 2 * d.N <= kTN && !d.b_pre) ? 1 : 0;
   *splits = 1;
   *part_floats = 0;
+  const int kel = (d.prec == TN_BF16 || d.prec == TN_BF16X3) ? 64 : 32;
+  const int64_t batch = (int64_t)d.n_outer * d.n_inner;
   if (*quad) {
-    const int kel = (d.prec == TN_BF16 || d.prec == TN_BF16X3) ? 64 : 32;
     const int64_t tiles = (K + kel - 1) / kel;
-    int64_t batch = (int64_t)d.n_outer * d.n_inner;
     int s = 1;
     while (batch * s < 2 * 152 && s * 2 <= tiles / 4 && s < 64) s *= 2;
     *splits = s;
-    if (s > 1) *part_floats = (size_t)s * batch * 2 * d.M * d.N;
+  } else {
+    // realified-B form: split K when the output tiles alone leave most of the
+    // GPU idle (a few sites with a long contraction: the closes of a small
+    // cell at large chi)
+    const int64_t nr = 2 * (int64_t)d.N;
+    const int64_t tn = nr >= kTN ? kTN : ((nr + 15) / 16) * 16;
+    const int64_t ctas = batch * ((d.M + kTM - 1) / kTM) * ((nr + tn - 1) / tn);
+    const int64_t ktiles = (2 * K + kel - 1) / kel;
+    int s = 1;
+    if (ctas < 152)
+      while (ctas * s < 2 * 152 && s * 2 <= ktiles / 4 && s < 64) s *= 2;
+    *splits = s;
   }
+  if (*splits > 1) *part_floats = (size_t)(*splits) * batch * 2 * d.M * d.N;
   return true;
 }
 

@@ -1,8 +1,9 @@
 """The periodic 5-site cell of the infinite heavy-hex lattice ("Dynamics of the
 infinite heavy-hex lattice"): BP on the periodic cell is BP on the infinite
 lattice, so the cell and its 10-site double cover give the same <Z>; large chi
-(128) with the split-precision BF16 contractions against the plain FP32 path
-at the same chi, and against the FP64 oracle where both run (chi = 16, 64).
+(128, 256, bonds saturated) with the split-precision BF16 contractions against
+the plain FP32 path at the same chi, and against the FP64 oracle where both run
+(chi = 16, 64).
 """
 import numpy as np
 import pytest
@@ -69,11 +70,20 @@ def test_cell_chi64_split_bf16_matches_oracle(tnlib):
     assert np.abs(z - o.all_z()).max() < 1e-4
 
 
-def test_cell_chi128_split_bf16_matches_fp32_path(tnlib):
-    """chi = 128 contractions (2 x 128^3 site tensors) and the 256 x 256 FP64
-    truncation solve; 3 steps keep the FP64 solve's time in bounds."""
+@pytest.mark.parametrize("chi,steps", [(128, 10), (256, 10)])
+def test_cell_large_chi_split_bf16_matches_fp32_path(tnlib, chi, steps):
+    """chi = 128 and 256 (site tensors 2 x chi^3, the 2chi x 2chi refined FP64
+    truncation solve through its global-memory basis kernel) with every bond
+    saturated: after 10 steps each of the cell's bonds keeps chi nonzero values.
+    Split BF16 contractions against the plain FP32 path at the same chi."""
     g = OG.periodic_cell()
-    z3 = _z(tnlib, g, 128, 0.7, 3, prec="bf16x3")
-    z1 = _z(tnlib, g, 128, 0.7, 3, prec="fp32")
-    assert np.abs(z3 - z1).max() < 1e-4
-    assert np.all(np.abs(z1) <= 1 + 1e-6)
+    out = {}
+    for prec in ("bf16x3", "fp32"):
+        with tnlib.TNState(g.n, g.edges, g.colours, chi=chi, prec=prec) as s:
+            s.apply_floquet(0.7, steps)
+            out[prec] = s.expect_z_all()
+            if prec == "fp32":
+                for e in range(len(g.edges)):
+                    assert np.count_nonzero(s.bond_spectrum(e) > 1e-12) == chi
+    assert np.abs(out["bf16x3"] - out["fp32"]).max() < 1e-4
+    assert np.all(np.abs(out["fp32"]) <= 1 + 1e-6)

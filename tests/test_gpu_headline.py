@@ -16,9 +16,12 @@ fixed point, where the residual floor of the precision (2e-6 FP32, 2e-5 BF16x3,
 2e-3 TF32, 2e-2 BF16) bounds how well the messages are determined
 (TF32: 2^-11 relative per operand, BF16: 2^-9; the split products leave about
 2^-21 and 2^-16).  Measured on GB300 (max over both steps): FP32 7.9e-7,
-TF32X3 8.7e-6, BF16X3 3.1e-5, TF32 1.8e-3, BF16 1.8e-2 in <Z>.  The spectra
-carry the absolute floor of about sqrt(eps) sigma_1 that FP32-rounded Gram
-inputs put under a singular value; they are compared at the bounds below.
+TF32X3 8.7e-6, BF16X3 3.1e-5, TF32 1.8e-3 and 3.2e-3 (two summation orders of
+the split-K partials), BF16 1.8e-2 in <Z>.  The spectra carry the absolute
+floor of about sqrt(eps_32) sigma_1 = 2.4e-4 sigma_1 that FP32-rounded Gram
+inputs put under a singular value (FP32 measured 1.6e-5 and 6.3e-5 under the
+two summation orders); their bounds are that floor, or the precision's own
+rounding where it is larger.
 
 The returned state is also checked for what every valid result has: unit
 Frobenius norm Hermitian PSD messages, Bloch vectors inside the unit ball, and
@@ -37,8 +40,8 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
                       "eagle127_chi64_theta0.9425.txt")
 THETA = float(np.linspace(0.0, np.pi / 2, 16)[9])
-Z_BOUND = {"fp32": 1e-6, "tf32x3": 3e-5, "bf16x3": 1e-4, "tf32": 3e-3, "bf16": 3e-2}
-S_BOUND = {"fp32": 5e-5, "tf32x3": 5e-4, "bf16x3": 1e-4, "tf32": 5e-3, "bf16": 5e-2}
+Z_BOUND = {"fp32": 1e-6, "tf32x3": 3e-5, "bf16x3": 1e-4, "tf32": 5e-3, "bf16": 3e-2}
+S_BOUND = {"fp32": 3e-4, "tf32x3": 5e-4, "bf16x3": 3e-4, "tf32": 5e-3, "bf16": 5e-2}
 FLOOR = {"fp32": 2e-6, "tf32x3": 2e-6, "bf16x3": 2e-5, "tf32": 2e-3, "bf16": 2e-2}
 
 
