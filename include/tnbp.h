@@ -231,6 +231,27 @@ tn_status tn_apply_clifford_dagger(tn_handle* h, int32_t steps);
 tn_status tn_bp_converge(tn_handle* h, double tol, int32_t max_iters,
                          int32_t* iters_out, double* residual_out);
 
+/*
+ * tn_bp_components — the connected components of the handle's graph (the
+ * instances of a disjoint union, see tn_apply_floquet_field) and what the last
+ * BP iteration did on each.  The stop rule of tn_bp_converge and of the
+ * regauging in tn_apply_floquet acts on every component separately: a
+ * component stops at its own tolerance (or FP32 residual floor, or max_iters)
+ * and its messages stay as they are while the others continue, so each
+ * instance receives the sweeps it would receive alone.
+ *   comp_of_vertex  n_vertices host int32 (may be NULL): component of each vertex,
+ *                   numbered in order of their smallest vertex.
+ *   sweeps_out      cap host int32 (may be NULL): sweeps of each component in
+ *                   the last BP iteration.
+ *   residual_out    cap host doubles (may be NULL): its final residual.
+ *   n_comp_out      number of components (may be NULL).
+ * Arrays are caller-owned; entries past min(cap, n_comp) are not written.
+ * Before the first BP iteration sweeps and residuals are 0.
+ * Errors: TN_EINVAL (null handle, cap < 0), TN_ECUDA.
+ */
+tn_status tn_bp_components(tn_handle* h, int32_t* comp_of_vertex, int32_t* sweeps_out,
+                           double* residual_out, int32_t cap, int32_t* n_comp_out);
+
 /* A Pauli string sign * prod_j P_{sites[j]}, P in {'X','Y','Z'}; sites distinct. */
 typedef struct {
   int32_t weight;

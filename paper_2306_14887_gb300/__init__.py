@@ -36,7 +36,7 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_server_poll_ex", "tn_server_wait_ex",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
            "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma",
-           "tn_bp_error", "tn_graph_info", "tn_selftest_bounded_wait"]
+           "tn_bp_error", "tn_graph_info", "tn_selftest_bounded_wait", "tn_bp_components"]
 
 
 class TNError(RuntimeError):
@@ -124,6 +124,7 @@ def lib():
         L.tn_apply_floquet.argtypes = [vp, C.c_double, i32]
         L.tn_apply_clifford_dagger.argtypes = [vp, i32]
         L.tn_bp_converge.argtypes = [vp, C.c_double, i32, C.POINTER(i32), dp]
+        L.tn_bp_components.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), dp, i32, C.POINTER(i32)]
         L.tn_expect.argtypes = [vp, C.POINTER(tn_pauli), i32, i32, dp]
         L.tn_expect_z_all.argtypes = [vp, dp]
         L.tn_get_stats.argtypes = [vp, C.POINTER(tn_stats)]
@@ -354,6 +355,20 @@ class TNState:
         if s not in (TN_OK, -3):
             _check(s)
         return it.value, res.value, s
+
+    def bp_components(self):
+        """(comp_of_vertex, sweeps, residuals) of the last BP iteration, per
+        connected component (instance of a disjoint union)."""
+        nc = C.c_int32()
+        _check(lib().tn_bp_components(self._h, None, None, None, 0, C.byref(nc)))
+        comp = np.zeros(self.n, dtype=np.int32)
+        sw = np.zeros(max(1, nc.value), dtype=np.int32)
+        res = np.zeros(max(1, nc.value), dtype=np.float64)
+        _check(lib().tn_bp_components(self._h, comp.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      sw.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      res.ctypes.data_as(C.POINTER(C.c_double)), nc.value,
+                                      C.byref(nc)))
+        return comp, sw[:nc.value], res[:nc.value]
 
     # ---------------------------------------------------------- expectations
     def expect_z_all(self):

@@ -156,9 +156,27 @@ cudaError_t launch_phys_gate(float* T, const int64_t* site_off, int n_sites, int
 // current ones: msg <- normalise(raw); residual <- max ||new - old||_F.
 // res_bits: one unsigned long long holding the max residual as IEEE bits;
 // flags: bit 0 set on a non-finite or zero-norm message.
+// Per-component state of the device-side BP stop rule (kernels.cu): the
+// component of each directed message, the per-component state
+// [previous residual, final residual, sweeps, done] and residual accumulator.
+struct BpComp {
+  const int* comp_of_msg = nullptr;
+  const double* state = nullptr;
+  unsigned long long* res = nullptr;
+};
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
                              unsigned long long* res_bits, int* flags, cudaStream_t s,
-                             float* mrt = nullptr);
+                             float* mrt = nullptr, const BpComp* comp = nullptr);
+// The device-side BP loop: reset the per-component state and the loop's
+// parameters; after each sweep, apply the stop rule per component and set the
+// while-loop condition (set_cond) or only the continue word out[4].
+cudaError_t launch_bp_loop_init(int n_comp, double* state, unsigned long long* res,
+                                unsigned long long* res_bits, double* par, double tol,
+                                int max_iters, double floor_, unsigned long long* out,
+                                cudaStream_t s);
+cudaError_t launch_bp_stop(int n_comp, double* state, unsigned long long* res,
+                           unsigned long long* res_bits, const double* par, unsigned long long* out,
+                           cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s);
 
 // Realified transposed copies of n planar complex chi x chi matrices (each at
 // src + i*src_stride): dst + i*4chi^2 holds Bt[(t,n)][(s,k)] as in GemmDesc::b_pre.

@@ -136,11 +136,24 @@ struct tn_handle {
   double* h_stats = nullptr;  // host copy of solve stats
   // one BP sweep captured as a CUDA graph (memset of the status words, the
   // contraction launches, normalisation, read-back of the status words)
-  cudaGraphExec_t sweep_exec = nullptr;
+  // The BP iteration runs on the device: a graph whose while-loop node repeats
+  // the sweep (contractions, normalisation, the stop-rule kernel) until every
+  // connected component of the graph has met the stop rule; the host waits
+  // once per regauge.
+  cudaGraphExec_t loop_exec = nullptr;
+  bool loop_unavailable = false;  // the driver refused the conditional node
   double sweep_flops = 0.0, sweep_bytes = 0.0;
   int64_t sweep_kernels = 0, sweep_tma = 0;  // launches inside the captured sweep
   size_t part_floats = 0;                     // size of the split-K partial buffer
-  unsigned long long* h_status = nullptr;  // pinned: [residual bits, flags]
+  unsigned long long* h_status = nullptr;  // pinned: the stop rule's 5 output words
+  // connected components (the instances of a disjoint union)
+  int n_comp = 0;
+  std::vector<int> comp_of_vertex;
+  int* comp_of_msg = nullptr;        // [2E] component of each directed message
+  double* comp_state = nullptr;      // [n_comp][4] prev residual, final residual, sweeps, done
+  unsigned long long* comp_res = nullptr;  // [n_comp] residual accumulator of a sweep
+  double* loop_par = nullptr;              // tol, max_iters, floor
+  unsigned long long* loop_out = nullptr;  // the stop rule's output words
 
   // per-kernel-class timing with CUDA events on the handle's stream
   bool prof_on = false;
@@ -1062,11 +1075,12 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
   return check_flags(h, "the truncation solve");
 }
 
-// Enqueue one sweep: clear the status words, contract, normalise (residual and
-// flags accumulate in the status words), copy them to pinned host memory.
-tn_status enqueue_sweep(tn_handle* h, bool fork = false) {
+// Enqueue one sweep: contract, normalise (the residual of every component
+// and the flags accumulate on the device), then the stop-rule kernel.  Inside
+// the device loop (`in_loop`) the stop kernel sets the while-loop condition;
+// otherwise its output words are copied to pinned host memory.
+tn_status enqueue_sweep(tn_handle* h, bool fork, bool in_loop, cudaGraphConditionalHandle cond = 0) {
   const int nmsg = 2 * (int)h->g.eu.size();
-  TN_CUDA_TRY(cudaMemsetAsync(h->res_bits, 0, 2 * sizeof(unsigned long long), h->stream));
   tn_status st;
   if (fork) {
     // degree-2 and degree-1 launches on the side stream, beside the degree-3 chains
@@ -1083,22 +1097,31 @@ tn_status enqueue_sweep(tn_handle* h, bool fork = false) {
     if (st) return st;
   }
   const int pi = prof_begin(h, P_NORM);
+  BpComp comp;
+  comp.comp_of_msg = h->comp_of_msg;
+  comp.state = h->comp_state;
+  comp.res = h->comp_res;
   TN_CUDA_TRY(launch_normalise(h->raw, h->msg, nmsg, h->chi, h->res_bits, h->flags, h->stream,
-                               h->mrt));
+                               h->mrt, &comp));
   prof_end(h, pi, 0.0, 3.0 * 8.0 * h->chi * h->chi * nmsg);
-  h->stats.kernel_launches++;
-  TN_CUDA_TRY(cudaMemcpyAsync(h->h_status, h->res_bits, 2 * sizeof(unsigned long long),
-                              cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(launch_bp_stop(h->n_comp, h->comp_state, h->comp_res, h->res_bits, h->loop_par,
+                             h->loop_out, cond, in_loop ? 1 : 0, h->stream));
+  h->stats.kernel_launches += 2;
+  if (!in_loop)
+    TN_CUDA_TRY(cudaMemcpyAsync(h->h_status, h->loop_out, 5 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, h->stream));
   return TN_OK;
 }
 
-// Capture enqueue_sweep into a graph (once, on a non-default stream).  While
-// profiling, the whole graph is timed as one bp_contract launch.
-tn_status sweep_graph(tn_handle* h, bool* use) {
+// Build (once, on a non-default stream) the device-side BP loop: a graph
+// holding one while-loop node whose body is the captured sweep.  The loop
+// condition starts at 1 and the stop-rule kernel at the end of each sweep
+// sets it; every component stops at max_iters at the latest, so the loop
+// ends after at most max_iters sweeps.
+tn_status loop_graph(tn_handle* h, bool* use) {
   *use = false;
-  if (!h->sweep_exec) {
-    if (!h->stream) return TN_OK;  // the legacy default stream cannot be captured
-    cudaGraph_t graph = nullptr;
+  if (!h->loop_exec) {
+    if (!h->stream || h->loop_unavailable) return TN_OK;  // the legacy default stream cannot be captured
     const bool prof = h->prof_on;
     h->prof_on = false;
     bool fork = h->sweep_split > 0 && h->sweep_split < h->sweep.L.size() &&
@@ -1112,98 +1135,138 @@ tn_status sweep_graph(tn_handle* h, bool* use) {
       }
     }
     fork = fork && h->side && h->ev_fork && h->ev_join;
-    TN_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    TN_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNode_t node = nullptr;
+    cudaGraphNodeParams cp = {};
+    cudaError_t ce = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = cond;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    }
+    if (ce != cudaSuccess) {
+      // a driver without conditional nodes: the host drives the loop
+      cudaGetLastError();
+      cudaGraphDestroy(graph);
+      h->loop_unavailable = true;
+      h->prof_on = prof;
+      return TN_OK;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ce = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      h->prof_on = prof;
+      TN_CUDA_TRY(ce);
+    }
     const int64_t launches = h->stats.kernel_launches, tma = h->stats.tma_launches;
-    tn_status st = enqueue_sweep(h, fork);
-    // the captured sweep's launch counts, charged once per graph launch
+    tn_status st = enqueue_sweep(h, fork, true, cond);
+    // the captured sweep's launch counts, charged once per sweep
     h->sweep_kernels = h->stats.kernel_launches - launches;
     h->sweep_tma = h->stats.tma_launches - tma;
     h->stats.kernel_launches = launches;
     h->stats.tma_launches = tma;
     h->prof_on = prof;
-    cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
-    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
-    TN_CUDA_TRY(ce);
-    ce = cudaGraphInstantiate(&h->sweep_exec, graph, 0);
+    cudaGraph_t captured = nullptr;
+    ce = cudaStreamEndCapture(h->stream, &captured);
+    if (st || ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      if (st) return st;
+      TN_CUDA_TRY(ce);
+    }
+    ce = cudaGraphInstantiate(&h->loop_exec, graph, 0);
     cudaGraphDestroy(graph);
     TN_CUDA_TRY(ce);
-    h->sweep_flops = h->sweep_bytes = 0.0;
-    for (auto& L : h->sweep.L) {
-      double f, b;
-      gemm_work(L.d, &f, &b);
-      h->sweep_flops += f;
-      h->sweep_bytes += b;
-      // a fused pair neither writes nor reads back its intermediate
-      if (L.sp.maps && L.sp.kind == 2) h->sweep_bytes -= 16.0 * L.d.M * L.d.N * L.d.n_outer;
-    }
   }
   *use = true;
   return TN_OK;
 }
 
+void sweep_work(tn_handle* h) {
+  if (h->sweep_flops > 0.0 || h->sweep_bytes > 0.0) return;
+  for (auto& L : h->sweep.L) {
+    double f, b;
+    gemm_work(L.d, &f, &b);
+    h->sweep_flops += f;
+    h->sweep_bytes += b;
+    // a fused pair neither writes nor reads back its intermediate
+    if (L.sp.maps && L.sp.kind == 2) h->sweep_bytes -= 16.0 * L.d.M * L.d.N * L.d.n_outer;
+  }
+}
+
 tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, double* res) {
-  const int nmsg = 2 * (int)h->g.eu.size();
   // Messages are stored in FP32: once the residual is down at the rounding
   // floor of the arithmetic it stops decreasing and only fluctuates.  Below
   // `floor`, a sweep whose residual is not below 0.98 of the previous one
   // (the floor's signature; slow but steady convergence keeps going), or a
   // residual under floor / 8, ends the iteration as converged: the FP64
-  // tolerance cannot be met by FP32 messages.
+  // tolerance cannot be met by FP32 messages.  The rule acts on every
+  // connected component separately (bp_stop_kernel), and a component that has
+  // stopped keeps its messages, so an instance of a disjoint union receives
+  // exactly the sweeps it would receive alone.
   const double floor = precision_floor(h);
-  double r = INFINITY;
-  std::vector<double> hist;
-  bool stagnated = false;
-  int it = 0;
   {
     tn_status st0 = ensure_ta(h);
     if (st0) return st0;
     st0 = ensure_mrt(h);
     if (st0) return st0;
   }
-  bool use_graph = false;
+  sweep_work(h);
+  bool use_loop = false;
   {
-    tn_status st0 = sweep_graph(h, &use_graph);
+    tn_status st0 = loop_graph(h, &use_loop);
     if (st0) return st0;
   }
-
-  for (it = 1; it <= max_iters; ++it) {
-    if (use_graph) {
-      const int pi = prof_begin(h, P_BP);
-      TN_CUDA_TRY(cudaGraphLaunch(h->sweep_exec, h->stream));
-      prof_end(h, pi, h->sweep_flops, h->sweep_bytes);
-    } else {
-      tn_status st = enqueue_sweep(h);
-      if (st) return st;
-    }
-    if (use_graph) {
-      h->stats.kernel_launches += h->sweep_kernels;
-      h->stats.tma_launches += h->sweep_tma;
-    }
+  if (max_iters < 1) max_iters = 1;
+  TN_CUDA_TRY(launch_bp_loop_init(h->n_comp, h->comp_state, h->comp_res, h->res_bits, h->loop_par,
+                                  tol, max_iters, floor, h->loop_out, h->stream));
+  h->stats.kernel_launches++;
+  int64_t sweeps = 0;
+  if (use_loop) {
+    const int pi = prof_begin(h, P_BP);
+    TN_CUDA_TRY(cudaGraphLaunch(h->loop_exec, h->stream));
+    prof_end(h, pi, 0.0, 0.0);
+    TN_CUDA_TRY(cudaMemcpyAsync(h->h_status, h->loop_out, 5 * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, h->stream));
     TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    const unsigned long long bits = h->h_status[0];
-    const int flags = (int)h->h_status[1];
-    memcpy(&r, &bits, sizeof(r));
-    if (flags) {
-      TN_CUDA_TRY(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
-      set_error(flags & 2 ? "a device-side wait gave up in a BP sweep"
-                          : "non-finite or zero-norm values detected in a BP sweep");
-      return flags & 2 ? TN_ETIMEOUT : TN_ENUMERIC;
+    sweeps = (int64_t)h->h_status[0];
+    if (pi >= 0) {
+      h->prof_pending[pi].flops = h->sweep_flops * sweeps;
+      h->prof_pending[pi].bytes = h->sweep_bytes * sweeps;
     }
-    if (r < tol) break;
-    hist.push_back(r);
-    const size_t k = hist.size();
-    if (r < floor && (r < floor / 8 || (k >= 2 && r >= 0.98 * hist[k - 2]))) {
-      stagnated = true;
-      break;
+    h->stats.kernel_launches += h->sweep_kernels * sweeps;
+    h->stats.tma_launches += h->sweep_tma * sweeps;
+  } else {
+    for (int it = 1; it <= max_iters; ++it) {
+      tn_status st = enqueue_sweep(h, false, false);
+      if (st) return st;
+      TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+      if (h->h_status[4] == 0) break;
     }
+    sweeps = (int64_t)h->h_status[0];
   }
-  if (it > max_iters) it = max_iters;
+  const int flags = (int)h->h_status[3];
+  double r;
+  const unsigned long long bits = h->h_status[1];
+  memcpy(&r, &bits, sizeof(r));
+  if (flags) {
+    TN_CUDA_TRY(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    set_error(flags & 2 ? "a device-side wait gave up in a BP sweep"
+                        : "non-finite or zero-norm values detected in a BP sweep");
+    return flags & 2 ? TN_ETIMEOUT : TN_ENUMERIC;
+  }
+  const int it = (int)sweeps;
   h->stats.bp_iters_last = it;
   h->stats.bp_iters_total += it;
   h->stats.bp_residual_last = r;
   if (iters) *iters = it;
   if (res) *res = r;
-  if (!(r < tol) && !stagnated) {
+  if (h->h_status[2] > 0) {
     set_error("BP did not reach the tolerance within max_iters");
     return TN_ENOTCONVERGED;
   }
@@ -1430,6 +1493,32 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   h->res_bits = (unsigned long long*)dev_alloc(h, 64);
   h->flags = h->res_bits ? reinterpret_cast<int*>(h->res_bits + 1) : nullptr;
+  {
+    // connected components by union-find over the edges
+    std::vector<int> root(g.n);
+    for (int v = 0; v < g.n; ++v) root[v] = v;
+    auto find = [&](int v) {
+      while (root[v] != v) v = root[v] = root[root[v]];
+      return v;
+    };
+    for (size_t e = 0; e < g.eu.size(); ++e) {
+      const int a = find(g.eu[e]), b = find(g.ew[e]);
+      if (a != b) root[std::max(a, b)] = std::min(a, b);
+    }
+    h->comp_of_vertex.assign(g.n, -1);
+    std::vector<int> id(g.n, -1);
+    h->n_comp = 0;
+    for (int v = 0; v < g.n; ++v) {
+      const int r = find(v);
+      if (id[r] < 0) id[r] = h->n_comp++;
+      h->comp_of_vertex[v] = id[r];
+    }
+  }
+  h->comp_of_msg = (int*)dev_alloc(h, sizeof(int) * std::max<size_t>(1, 2 * g.eu.size()));
+  h->comp_state = (double*)dev_alloc(h, sizeof(double) * 4 * std::max(1, h->n_comp));
+  h->comp_res = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * std::max(1, h->n_comp));
+  h->loop_par = (double*)dev_alloc(h, sizeof(double) * 4);
+  h->loop_out = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 8);
   h->rho = (double*)dev_alloc(h, sizeof(double) * 8 * g.n);
   h->rho_part = (double*)dev_alloc(h, sizeof(double) * 16 * 8 * std::max(1, g.n));
   for (int d = 1, base = 0; d <= 3; ++d) {
@@ -1452,6 +1541,7 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   if (!h->T || !h->Ts || !h->Y1 || !h->Y2 || !h->TA || !h->mrt || !h->drt || !h->msg ||
       !h->raw || !h->gram || !h->dmat ||
       !h->work || !h->solve_stats || !h->res_bits || !h->flags || !h->rho || !h->rho_part ||
+      !h->comp_of_msg || !h->comp_state || !h->comp_res || !h->loop_par || !h->loop_out ||
       !h->rx_cs ||
       !h->spectra) {
     set_error("device allocation failed (footprint " + std::to_string(footprint_of(g, chi)) +
@@ -1480,8 +1570,18 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
       return fail(TN_ECUDA);
     }
   }
+  {
+    std::vector<int> cm(2 * g.eu.size());
+    for (size_t e = 0; e < g.eu.size(); ++e) cm[2 * e] = cm[2 * e + 1] = h->comp_of_vertex[g.eu[e]];
+    if (!cm.empty() && cudaMemcpy(h->comp_of_msg, cm.data(), sizeof(int) * cm.size(),
+                                  cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("upload of the component table failed");
+      return fail(TN_ECUDA);
+    }
+  }
   cudaMemset(h->res_bits, 0, 64);
-  if (cudaMallocHost(&h->h_status, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+  cudaMemset(h->comp_state, 0, sizeof(double) * 4 * std::max(1, h->n_comp));
+  if (cudaMallocHost(&h->h_status, 8 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     set_error("pinned host allocation failed");
     delete[] h->h_stats;
@@ -1534,7 +1634,7 @@ tn_status tn_destroy(tn_handle* h) {
   if (!h) return TN_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
-  if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -1632,6 +1732,26 @@ tn_status tn_bp_converge(tn_handle* h, double tol, int32_t max_iters, int32_t* i
   if (iters_out) *iters_out = it;
   if (residual_out) *residual_out = r;
   return st;
+}
+
+tn_status tn_bp_components(tn_handle* h, int32_t* comp_of_vertex, int32_t* sweeps_out,
+                           double* residual_out, int32_t cap, int32_t* n_comp_out) {
+  if (!h || cap < 0) { set_error("null handle or cap < 0"); return TN_EINVAL; }
+  if (n_comp_out) *n_comp_out = h->n_comp;
+  if (comp_of_vertex)
+    for (int v = 0; v < h->g.n; ++v) comp_of_vertex[v] = h->comp_of_vertex[v];
+  const int m = std::min(cap, h->n_comp);
+  if ((sweeps_out || residual_out) && m > 0) {
+    std::vector<double> st(4 * (size_t)h->n_comp);
+    TN_CUDA_TRY(cudaMemcpyAsync(st.data(), h->comp_state, sizeof(double) * st.size(),
+                                cudaMemcpyDeviceToHost, h->stream));
+    TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < m; ++c) {
+      if (sweeps_out) sweeps_out[c] = (int32_t)st[4 * c + 2];
+      if (residual_out) residual_out[c] = st[4 * c + 1];
+    }
+  }
+  return TN_OK;
 }
 
 tn_status tn_expect_z_all(tn_handle* h, double* out) {

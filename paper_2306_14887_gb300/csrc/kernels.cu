@@ -309,8 +309,11 @@ __device__ __forceinline__ void pair_add_sq(float& s, float& c, float a) {
 
 // Large chi: the transposed entry is read from global memory.
 __global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
-                                      unsigned long long* res_bits, int* flags) {
+                                      unsigned long long* res_bits, int* flags, BpComp comp) {
   __shared__ double sh[32];
+  // a message of a component that has already converged stays as it is
+  const int cmp = comp.comp_of_msg ? comp.comp_of_msg[blockIdx.x] : -1;
+  if (cmp >= 0 && comp.state[4 * cmp + 3] != 0.0) return;
   const int64_t n2 = (int64_t)chi * chi;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float* r = raw + blockIdx.x * 2 * n2;
@@ -346,6 +349,7 @@ __global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
   if (threadIdx.x == 0) {
     const double res = sqrt(dd);
     atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
+    if (cmp >= 0) atomicMax(&comp.res[cmp], (unsigned long long)__double_as_longlong(res));
   }
 }
 
@@ -353,8 +357,12 @@ __global__ void normalise_gmem_kernel(const float* raw, float* msg, int chi,
 // transposed entry needed by the Hermitisation is a shared-memory read.
 __global__ void normalise_kernel(const float* __restrict__ raw, float* __restrict__ msg, int chi,
                                  unsigned long long* res_bits, int* flags,
-                                 float* __restrict__ mrt) {
+                                 float* __restrict__ mrt, BpComp comp) {
   __shared__ double sh[32];
+  // a message of a component that has already converged stays as it is (and
+  // so does its realified copy)
+  const int cmp = comp.comp_of_msg ? comp.comp_of_msg[blockIdx.x] : -1;
+  if (cmp >= 0 && comp.state[4 * cmp + 3] != 0.0) return;
   // re and im planes of the new message, chi x (chi + 1) each (padded rows for
   // the transposed reads), then the old message's two planes, chi x chi each
   extern __shared__ float sraw[];
@@ -422,6 +430,103 @@ __global__ void normalise_kernel(const float* __restrict__ raw, float* __restric
   if (threadIdx.x == 0) {
     const double res = sqrt(dd);
     atomicMax(res_bits, (unsigned long long)__double_as_longlong(res));
+    if (cmp >= 0) atomicMax(&comp.res[cmp], (unsigned long long)__double_as_longlong(res));
+  }
+}
+
+// ------------------------------------------------------------------------
+// The BP stop rule on the device, per connected component of the handle's
+// graph (one instance of a batch union): component c stops after a sweep
+// whose residual r_c (the largest ||M_new - M_old||_F of its messages) is
+// below tol; or, once r_c is below the precision's residual floor, when r_c is
+// under floor / 8 or not below 0.98 of its previous sweep's (FP32 messages
+// cannot reach an FP64 tolerance); or at max_iters.  A stopped component's
+// messages are frozen (the normalise kernels skip them), so it keeps exactly
+// the messages it would have had alone.  state[4c..4c+3]: previous residual,
+// final residual, sweeps, done.  out: [0] the largest sweep count, [1] the
+// largest final residual (IEEE bits), [2] components stopped at max_iters
+// without converging, [3] the flag word, [4] 1 while any component runs.
+__global__ void bp_loop_init_kernel(int n_comp, double* state, unsigned long long* res,
+                                    unsigned long long* res_bits, double* par, double tol,
+                                    double max_iters, double floor_, unsigned long long* out) {
+  for (int c = threadIdx.x; c < n_comp; c += blockDim.x) {
+    state[4 * c + 0] = INFINITY;
+    state[4 * c + 1] = 0.0;
+    state[4 * c + 2] = 0.0;
+    state[4 * c + 3] = 0.0;
+    res[c] = 0ull;
+  }
+  if (threadIdx.x == 0) {
+    res_bits[0] = 0ull;
+    res_bits[1] = 0ull;  // the flag word shares this 8-byte slot
+    par[0] = tol;
+    par[1] = max_iters;
+    par[2] = floor_;
+    for (int i = 0; i < 5; ++i) out[i] = 0ull;
+  }
+}
+
+__global__ void bp_stop_kernel(int n_comp, double* state, unsigned long long* res,
+                               unsigned long long* res_bits, const double* par,
+                               unsigned long long* out, cudaGraphConditionalHandle cond,
+                               int set_cond) {
+  __shared__ double smax[2];
+  __shared__ int cnt[2];
+  const int flags = *reinterpret_cast<const int*>(res_bits + 1);
+  const double tol = par[0], max_iters = par[1], floor_ = par[2];
+  if (threadIdx.x == 0) { smax[0] = 0.0; smax[1] = 0.0; cnt[0] = 0; cnt[1] = 0; }
+  __syncthreads();
+  int active = 0;
+  for (int c = threadIdx.x; c < n_comp; c += blockDim.x) {
+    if (state[4 * c + 3] == 0.0) {
+      const double r = __longlong_as_double((long long)res[c]);
+      const double it = state[4 * c + 2] + 1.0;
+      const double prev = state[4 * c + 0];
+      const bool conv = r < tol;
+      const bool stag = !conv && r < floor_ && (r < floor_ / 8 || (it >= 2.0 && r >= 0.98 * prev));
+      const bool cap = it >= max_iters;
+      state[4 * c + 2] = it;
+      state[4 * c + 0] = r;
+      if (conv || stag || cap || flags) {
+        state[4 * c + 3] = 1.0;
+        state[4 * c + 1] = r;
+        if (!conv && !stag) atomicAdd(&cnt[1], 1);
+      } else {
+        active = 1;
+      }
+    }
+    res[c] = 0ull;  // the next sweep's accumulator
+  }
+  active = __syncthreads_or(active);
+  if (!active) {
+    // the loop ends: summary over every component
+    double ms = 0.0, mr = 0.0;
+    for (int c = threadIdx.x; c < n_comp; c += blockDim.x) {
+      ms = fmax(ms, state[4 * c + 2]);
+      mr = fmax(mr, state[4 * c + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ms = fmax(ms, __shfl_xor_sync(0xffffffffu, ms, o));
+      mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(reinterpret_cast<unsigned long long*>(&smax[0]),
+                (unsigned long long)__double_as_longlong(ms));
+      atomicMax(reinterpret_cast<unsigned long long*>(&smax[1]),
+                (unsigned long long)__double_as_longlong(mr));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!active) {
+      out[0] = (unsigned long long)smax[0];
+      out[1] = (unsigned long long)__double_as_longlong(smax[1]);
+    }
+    out[2] += (unsigned long long)cnt[1];
+    out[3] = (unsigned long long)(unsigned)flags;
+    out[4] = active ? 1ull : 0ull;
+    res_bits[0] = 0ull;
+    if (set_cond) cudaGraphSetConditional(cond, active ? 1u : 0u);
   }
 }
 
@@ -586,12 +691,30 @@ cudaError_t normalise_prepare(int) {
   return result;
 }
 
+cudaError_t launch_bp_loop_init(int n_comp, double* state, unsigned long long* res,
+                                unsigned long long* res_bits, double* par, double tol,
+                                int max_iters, double floor_, unsigned long long* out,
+                                cudaStream_t s) {
+  bp_loop_init_kernel<<<1, 256, 0, s>>>(n_comp, state, res, res_bits, par, tol, (double)max_iters,
+                                        floor_, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bp_stop(int n_comp, double* state, unsigned long long* res,
+                           unsigned long long* res_bits, const double* par, unsigned long long* out,
+                           cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
+  bp_stop_kernel<<<1, 256, 0, s>>>(n_comp, state, res, res_bits, par, out, cond, set_cond);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
-                             unsigned long long* res_bits, int* flags, cudaStream_t s, float* mrt) {
+                             unsigned long long* res_bits, int* flags, cudaStream_t s, float* mrt,
+                             const BpComp* comp) {
   if (n_msgs <= 0) return cudaSuccess;
+  const BpComp cp = comp ? *comp : BpComp{};
   const size_t sm = sizeof(float) * 2 * (size_t)chi * (chi + 1) + sizeof(float) * 2 * (size_t)chi * chi;
   if (sm > 200 * 1024) {
-    normalise_gmem_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags);
+    normalise_gmem_kernel<<<n_msgs, 256, 0, s>>>(raw, msg, chi, res_bits, flags, cp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !mrt) return e;
     return launch_realify(msg, 2 * (int64_t)chi * chi, mrt, n_msgs, chi, s);
@@ -600,7 +723,7 @@ cudaError_t launch_normalise(const float* raw, float* msg, int n_msgs, int chi,
     cudaError_t e = normalise_prepare(chi);
     if (e != cudaSuccess) return e;
   }
-  normalise_kernel<<<n_msgs, 256, sm, s>>>(raw, msg, chi, res_bits, flags, mrt);
+  normalise_kernel<<<n_msgs, 256, sm, s>>>(raw, msg, chi, res_bits, flags, mrt, cp);
   return cudaGetLastError();
 }
 

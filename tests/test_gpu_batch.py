@@ -3,10 +3,11 @@ with its own kick angle, evolved as one handle over their disjoint union.
 
 BP and the simple update never couple components of a graph, so each instance
 evolves as it would alone; the union only changes how the work is launched
-(every contraction of every instance in the same launches, one CUDA graph per
-BP sweep).  The BP stop rule acts on the largest residual over the union, so an
-instance may receive sweeps beyond its own stopping point: at the FP32 floor
-these move <Z> by well under the FP32 parity bound of 1e-6.
+(every contraction of every instance in the same launches, the whole BP
+iteration as one device-side loop).  The BP stop rule acts on every connected
+component separately and a component that has stopped keeps its messages, so
+an instance's result does not depend on its batch-mates: changing another
+instance leaves it bit-identical.
 """
 import numpy as np
 import pytest
@@ -83,3 +84,65 @@ def test_field_with_uniform_angle_equals_scalar_kick(tnlib):
         a.apply_floquet(0.7, 4)
         b.apply_floquet_field(np.full(g.n, 0.7), 4)
         assert np.abs(a.expect_z_all() - b.expect_z_all()).max() < 1e-6
+
+
+def test_batch_mates_do_not_change_an_instance(tnlib):
+    """Two unions that differ only in the angle of instance 0: every other
+    instance gets bit-identical <Z> and the same per-component sweep counts."""
+    insts = _instances(6, seed=11)
+    chi, steps = 8, 4          # truncation at step 4 (2^4 > 8)
+    n, edges, cols, offs = tnlib.batch_union([(g.n, g.edges, g.colours) for g, _ in insts])
+    th = np.concatenate([np.full(g.n, t) for g, t in insts])
+    th2 = th.copy()
+    th2[:insts[0][0].n] = 0.31
+    out = []
+    for thetas in (th, th2):
+        with tnlib.TNState(n, edges, cols, chi=chi, prec="fp32") as s:
+            s.apply_floquet_field(thetas, steps)
+            z = s.expect_z_all()
+            comp, sweeps, res = s.bp_components()
+            assert s.stats()["bp_iters_last"] == sweeps.max()
+        out.append((z, comp, sweeps, res))
+    (z1, comp, sw1, r1), (z2, _, sw2, r2) = out
+    assert len(sw1) == len(insts)
+    for i, ((g, _), off) in enumerate(zip(insts, offs)):
+        assert np.all(comp[off:off + g.n] == i)
+        if i == 0:
+            continue
+        assert np.array_equal(z1[off:off + g.n], z2[off:off + g.n])
+        assert sw1[i] == sw2[i] and r1[i] == r2[i]
+    # instance 0 itself did change
+    assert np.abs(z1[:insts[0][0].n] - z2[:insts[0][0].n]).max() > 1e-3
+
+
+def test_component_sweeps_follow_each_instance(tnlib):
+    """An instance at theta = 0 (a product state, BP exact after one sweep)
+    stops long before its batch-mates, which need many sweeps."""
+    g = OG.eagle127()
+    n, edges, cols, offs = tnlib.batch_union([(g.n, g.edges, g.colours)] * 2)
+    thetas = np.concatenate([np.zeros(g.n), np.full(g.n, 0.9)])
+    with tnlib.TNState(n, edges, cols, chi=16, prec="fp32") as s:
+        s.apply_floquet_field(thetas, 5)
+        _, sweeps, res = s.bp_components()
+        z = s.expect_z_all()
+    assert sweeps[0] <= 2 < sweeps[1]
+    assert np.abs(z[:g.n] - 1.0).max() < 1e-6
+    with tnlib.TNState(g.n, g.edges, g.colours, chi=16, prec="fp32") as a:
+        a.apply_floquet(0.9, 5)
+        # two FP32 runs, each within 1e-6 of the FP64 oracle, whose launches
+        # split their sums differently (split-K follows the grid size)
+        assert np.abs(a.expect_z_all() - z[g.n:]).max() < 2e-6
+
+
+def test_device_loop_equals_host_loop(tnlib):
+    """The device-side BP loop (a graph with a while-loop node, on a stream of
+    the handle's own) and the host-driven loop (the legacy default stream,
+    which cannot be captured) apply the same stop rule to the same sweeps."""
+    g = OG.eagle127()
+    res = []
+    for stream in (None, 0):
+        with tnlib.TNState(g.n, g.edges, g.colours, chi=8, prec="fp32", stream=stream) as s:
+            s.apply_floquet(0.8, 6)
+            res.append((s.expect_z_all(), s.stats()["bp_iters_total"]))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
