@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--serve-jobs", type=int, default=16,
                    help="jobs of the serving leg (0: skip)")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched 64-instance leg")
     p.add_argument("--config4", action="store_true",
                    help="also run the large-chi periodic-cell leg (chi 128 and 256, 50 steps, "
                         "theta 0.4 / 0.7 / 1.0, BF16X3 against FP32) and print its own line")
@@ -169,6 +171,91 @@ def serve_leg(tn, args):
             "sample": "first %d jobs of the seeded stream with <= 127 qubits and chi <= 64 "
                       "(27- and 127-qubit graphs, chi 16/32/64, 5-20 steps), prec %s"
                       % (len(lat), args.prec)}
+
+
+def read_batched_golden():
+    """The FP64 oracle's <Z_v> for the covered instances of the batched
+    workload (tests/golden/batched64_oracle.txt, written by a script that calls
+    only oracle/): {index: (min_gap, z)}."""
+    path = os.path.join(ROOT, "tests", "golden", "batched64_oracle.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    gap = {}
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "inst":
+            kv = dict(zip(f[2::2], f[3::2]))
+            gap[int(f[1])] = float(kv["min_gap"])
+        elif f[0] == "Z":
+            i = int(f[1])
+            out[i] = (gap[i], np.array([float(x) for x in f[2:]]))
+    return out
+
+
+def batch_leg(tn, args):
+    """The batched workload: 64 seeded instances (27/65/127/433 qubits, chi from
+    {8, 16, 32, 64}, theta_h ~ U[0, pi/2], 10 steps) as one union handle per chi,
+    the four handles driven concurrently (tn.Batch).  Reports instance-steps/s
+    of the batch and of the same instances run one by one, and per instance
+    the <Z> error against its alone run and against the FP64 oracle (where the
+    golden file covers it)."""
+    import torch
+    from workloads import batched_jobs
+    graphs = {27: None, 65: tn.heavy_hex(5, 11), 127: eagle(), 433: tn.heavy_hex(13, 27)}
+    n, edges, cols = graphs[127]
+    keep = np.all(edges < 27, axis=1)
+    graphs[27] = (27, edges[keep], cols[keep])
+    jobs = batched_jobs(n=64)
+    steps = jobs[0][3]
+    insts = [graphs[size] + (chi, theta) for (size, chi, theta, _st) in jobs]
+    # warm-up: the same batch for one step (module loading, graph capture paths)
+    with tn.Batch(insts, prec=args.prec, solve=args.solve) as b:
+        b.evolve(1)
+    torch.cuda.synchronize()
+    with tn.Batch(insts, prec=args.prec, solve=args.solve) as b:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.evolve(steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        zb = b.expect_z()
+        sweeps = b.bp_sweeps()
+    alone_s, d_alone = 0.0, []
+    for (gn, ge, gc, chi, theta), z in zip(insts, zb):
+        stream = torch.cuda.Stream()
+        with tn.TNState(gn, ge, gc, chi=chi, prec=args.prec, stream=stream, solve=args.solve) as a:
+            stream.synchronize()
+            t0 = time.perf_counter()
+            a.apply_floquet(theta, steps)
+            stream.synchronize()
+            alone_s += time.perf_counter() - t0
+            d_alone.append(float(np.abs(a.expect_z_all() - z).max()))
+    gold = read_batched_golden()
+    d_oracle = [None] * len(jobs)
+    near_tie = []
+    for i, (gap, zo) in gold.items():
+        d_oracle[i] = float(np.abs(zb[i] - zo).max())
+        if gap <= 1e-6:
+            near_tie.append(i)
+    cov = [d for d in d_oracle if d is not None]
+    return {"instances": len(jobs), "steps": steps,
+            "instance_steps_per_s": round(len(jobs) * steps / wall, 3),
+            "wall_s": round(wall, 3),
+            "alone_instance_steps_per_s": round(len(jobs) * steps / alone_s, 3),
+            "groups": "one union handle per chi (8, 16, 32, 64), driven concurrently",
+            "max_dz_vs_alone": max(d_alone),
+            "dz_vs_alone": [float("%.3g" % d) for d in d_alone],
+            "oracle_covered": len(cov),
+            "max_dz_vs_oracle": max(cov) if cov else None,
+            "dz_vs_oracle": [None if d is None else float("%.3g" % d) for d in d_oracle],
+            "oracle_near_ties": near_tie,
+            "bp_sweeps_last": [int(x) for x in sweeps],
+            "prec": args.prec,
+            "note": "oracle values from tests/golden/batched64_oracle.txt (FP64 oracle on every "
+                    "instance with chi <= 16, chi = 32 up to 127 qubits, chi = 64 at 27 qubits)"}
 
 
 def config4_leg(tn, args):
@@ -527,6 +614,9 @@ def run_ours(args, rank, world, local):
     serving = None
     if args.serve_jobs > 0 and rank == 0:
         serving = serve_leg(tn, args)
+    batched = None
+    if not args.no_batch and rank == 0:
+        batched = batch_leg(tn, args)
     fp32_line = None
     if args.fp32_steps > 0 and args.prec != "fp32":
         s3 = tn.TNState(n, edges, cols, chi=chi, prec="fp32", stream=stream, solve=args.solve)
@@ -571,7 +661,7 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "z_mean": float(np.mean(z)),
         "fp32_path": fp32_line,
-        "serving": serving,
+        "serving": serving, "batched": batched,
     }
     if fp32_line:
         fp32_line["mixed_over_fp32"] = round(value / world / fp32_line["value"], 3)

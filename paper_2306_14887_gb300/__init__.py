@@ -513,6 +513,83 @@ def batch_union(instances):
     return n, np.concatenate(es), np.concatenate(cs), offs
 
 
+class Batch:
+    """Many independent instances of uneven size, kick angle and chi evolved
+    together: one disjoint-union handle per chi (BP and the simple update never
+    couple components, and the BP stop rule acts on each component alone, so
+    an instance's result does not depend on its batch-mates), the handles
+    driven concurrently by one host thread and CUDA stream each, so that the
+    groups' kernels overlap on the device.
+
+    instances: list of (n, edges, colours, chi, theta_h)."""
+
+    def __init__(self, instances, prec="tf32", solve="auto", **kw):
+        self.sizes = [int(inst[0]) for inst in instances]
+        groups = {}
+        for i, inst in enumerate(instances):
+            groups.setdefault(int(inst[3]), []).append(i)
+        self.groups = []
+        try:
+            for chi, idx in sorted(groups.items()):
+                n, e, c, offs = batch_union([tuple(instances[i][:3]) for i in idx])
+                th = np.concatenate([np.full(self.sizes[i], float(instances[i][4])) for i in idx])
+                st = TNState(n, e, c, chi=chi, prec=prec, solve=solve, **kw)
+                self.groups.append((chi, idx, offs, th, st))
+        except Exception:
+            self.close()
+            raise
+
+    def evolve(self, steps):
+        """`steps` Floquet steps of every instance (each group's handle on its
+        own host thread; the library releases the interpreter lock)."""
+        import threading
+        errs = []
+
+        def run(g):
+            try:
+                g[4].apply_floquet_field(g[3], steps)
+            except Exception as ex:  # re-raised on the caller's thread
+                errs.append(ex)
+
+        threads = [threading.Thread(target=run, args=(g,)) for g in self.groups]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errs:
+            raise errs[0]
+
+    def expect_z(self):
+        """<Z_v> of every instance, in input order."""
+        out = [None] * len(self.sizes)
+        for _chi, idx, offs, _th, st in self.groups:
+            z = st.expect_z_all()
+            for i, off in zip(idx, offs):
+                out[i] = z[off:off + self.sizes[i]]
+        return out
+
+    def bp_sweeps(self):
+        """Sweeps of every instance in its last BP iteration, in input order."""
+        out = np.zeros(len(self.sizes), dtype=np.int32)
+        for _chi, idx, offs, _th, st in self.groups:
+            comp, sw, _res = st.bp_components()
+            for i, off in zip(idx, offs):
+                # an instance's largest component count (a connected instance has one)
+                out[i] = sw[np.unique(comp[off:off + self.sizes[i]])].max()
+        return out
+
+    def close(self):
+        for g in self.groups:
+            g[4].close()
+        self.groups = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Server:
     """Continuous-batching job server on one device (see tn_server_* in tnbp.h)."""
 

@@ -146,3 +146,47 @@ def test_device_loop_equals_host_loop(tnlib):
             res.append((s.expect_z_all(), s.stats()["bp_iters_total"]))
     assert np.array_equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]
+
+
+def _read_batched_golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "batched64_oracle.txt")
+    rows, gap = {}, {}
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "inst":
+            kv = dict(zip(f[2::2], f[3::2]))
+            gap[int(f[1])] = (int(kv["size"]), int(kv["chi"]), float(kv["theta"]),
+                              int(kv["steps"]), float(kv["min_gap"]))
+        else:
+            rows[int(f[1])] = np.array([float(x) for x in f[2:]])
+    return {i: gap[i] + (rows[i],) for i in rows}
+
+
+def test_batched64_matches_oracle_golden(tnlib):
+    """The batched 64-instance workload (10 steps; sizes 27-433, chi 8-64,
+    seeded angles) on the instances the FP64 oracle covers, run as one union
+    handle per chi, concurrently (tn.Batch), in FP32: every instance within
+    1e-6 of the oracle where no truncation of its run was a near-tie."""
+    gold = _read_batched_golden()
+    assert len(gold) >= 40
+    idx = sorted(gold)
+    insts = []
+    for i in idx:
+        size, chi, theta, steps, _gap, _z = gold[i]
+        g = GRAPHS[size]()
+        insts.append((g.n, g.edges, g.colours, chi, theta))
+    steps = gold[idx[0]][3]
+    with tnlib.Batch(insts, prec="fp32") as b:
+        b.evolve(steps)
+        zs = b.expect_z()
+    checked = 0
+    for i, z in zip(idx, zs):
+        size, chi, theta, _steps, gap, want = gold[i]
+        assert np.all(np.abs(z) <= 1 + 1e-6)
+        if gap > 1e-6:
+            assert np.abs(z - want).max() < 1e-6, (i, size, chi, theta)
+            checked += 1
+    assert checked >= len(idx) // 2
