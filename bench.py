@@ -73,8 +73,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--serve-jobs", type=int, default=16,
                    help="jobs of the serving leg (0: skip)")
+    p.add_argument("--serve-mix", type=int, default=0,
+                   help="jobs of the full-mix serving leg (all sizes and chi; 0: skip)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched 64-instance leg")
+    p.add_argument("--batch-prec", default="tf32,tf32x3",
+                   help="comma-separated precisions of the batched leg")
     p.add_argument("--config4", action="store_true",
                    help="also run the large-chi periodic-cell leg (chi 128 and 256, 50 steps, "
                         "theta 0.4 / 0.7 / 1.0, BF16X3 against FP32) and print its own line")
@@ -173,6 +177,74 @@ def serve_leg(tn, args):
                       % (len(lat), args.prec)}
 
 
+def read_serving_golden():
+    """{job index: (min_gap, z)} of the FP64 oracle's seeded serving sample
+    (tests/golden/serving_sample_oracle.txt, written by a script that calls
+    only oracle/)."""
+    path = os.path.join(ROOT, "tests", "golden", "serving_sample_oracle.txt")
+    out, gap = {}, {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "job":
+            kv = dict(zip(f[2::2], f[3::2]))
+            gap[int(f[1])] = float(kv["min_gap"])
+        elif f[0] == "Z":
+            i = int(f[1])
+            out[i] = (gap[i], np.array([float(x) for x in f[2:]]))
+    return out
+
+
+def serve_mix_leg(tn, args):
+    """The serving workload at its stated mix: the first --serve-mix jobs of the
+    seeded Poisson stream (200 jobs/s; 27, 127, 433 and 1121 qubits; chi 16,
+    32, 64 and 128; 5-20 steps) submitted at their arrival times to a server
+    with 8 slots admitting by HBM footprint.  Latency is arrival to result;
+    the <Z> error against the FP64 oracle on the seeded 2% sample of the jobs
+    with at most 127 qubits and chi at most 64."""
+    from workloads import serving_jobs
+    n, edges, cols = eagle()
+    keep = np.all(edges < 27, axis=1)
+    graphs = {27: (27, edges[keep], cols[keep]), 127: (n, edges, cols),
+              433: tn.heavy_hex(13, 27), 1121: tn.heavy_hex(21, 43)}
+    stream = serving_jobs(n=2000)[:args.serve_mix]
+    gold = read_serving_golden()
+    lat, steps_done, dz = [], 0, {}
+    by_kind = {}
+    with tn.Server(slots=8) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for (arr, size, chi, theta, steps) in stream:
+            while time.perf_counter() - t0 < arr - stream[0][0]:
+                time.sleep(0.0005)
+            gn, ge, gc = graphs[size]
+            tickets.append(srv.submit(gn, ge, gc, chi, theta, steps, prec=args.prec))
+        for i, t in enumerate(tickets):
+            z, info = srv.wait(t)
+            lat.append(info["latency_s"])
+            steps_done += info["steps_done"]
+            by_kind.setdefault("%dq" % stream[i][1], []).append(info["latency_s"])
+            if i in gold:
+                dz[i] = float(np.abs(np.asarray(z) - gold[i][1]).max())
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.array(lat)
+    return {"jobs": len(lat), "slots": 8, "arrival_rate_per_s": 200.0,
+            "p50_s": round(float(np.percentile(lat, 50)), 3),
+            "p99_s": round(float(np.percentile(lat, 99)), 3),
+            "p50_s_by_size": {k: round(float(np.percentile(v, 50)), 3) for k, v in by_kind.items()},
+            "steps_per_s": round(steps_done / wall, 3), "wall_s": round(wall, 2),
+            "peak_resident": st["peak_resident"], "prec": args.prec,
+            "oracle_dz": {str(k): float("%.3g" % v) for k, v in dz.items()},
+            "oracle_min_gap": {str(k): float("%.3g" % gold[k][0]) for k in dz},
+            "sample": "first %d jobs of the seeded stream, every size and chi; oracle on the "
+                      "seeded 2%% sample of jobs with <= 127 qubits and chi <= 64 "
+                      "(tests/golden/serving_sample_oracle.txt)" % len(lat)}
+
+
 def read_batched_golden():
     """The FP64 oracle's <Z_v> for the covered instances of the batched
     workload (tests/golden/batched64_oracle.txt, written by a script that calls
@@ -196,6 +268,11 @@ def read_batched_golden():
 
 
 def batch_leg(tn, args):
+    """The batched workload in each precision of --batch-prec (see batch_run)."""
+    return {prec: batch_run(tn, args, prec) for prec in args.batch_prec.split(",") if prec}
+
+
+def batch_run(tn, args, prec):
     """The batched workload: 64 seeded instances (27/65/127/433 qubits, chi from
     {8, 16, 32, 64}, theta_h ~ U[0, pi/2], 10 steps) as one union handle per chi,
     the four handles driven concurrently (tn.Batch).  Reports instance-steps/s
@@ -212,10 +289,10 @@ def batch_leg(tn, args):
     steps = jobs[0][3]
     insts = [graphs[size] + (chi, theta) for (size, chi, theta, _st) in jobs]
     # warm-up: the same batch for one step (module loading, graph capture paths)
-    with tn.Batch(insts, prec=args.prec, solve=args.solve) as b:
+    with tn.Batch(insts, prec=prec, solve=args.solve) as b:
         b.evolve(1)
     torch.cuda.synchronize()
-    with tn.Batch(insts, prec=args.prec, solve=args.solve) as b:
+    with tn.Batch(insts, prec=prec, solve=args.solve) as b:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b.evolve(steps)
@@ -226,7 +303,7 @@ def batch_leg(tn, args):
     alone_s, d_alone = 0.0, []
     for (gn, ge, gc, chi, theta), z in zip(insts, zb):
         stream = torch.cuda.Stream()
-        with tn.TNState(gn, ge, gc, chi=chi, prec=args.prec, stream=stream, solve=args.solve) as a:
+        with tn.TNState(gn, ge, gc, chi=chi, prec=prec, stream=stream, solve=args.solve) as a:
             stream.synchronize()
             t0 = time.perf_counter()
             a.apply_floquet(theta, steps)
@@ -253,7 +330,7 @@ def batch_leg(tn, args):
             "dz_vs_oracle": [None if d is None else float("%.3g" % d) for d in d_oracle],
             "oracle_near_ties": near_tie,
             "bp_sweeps_last": [int(x) for x in sweeps],
-            "prec": args.prec,
+            "prec": prec,
             "note": "oracle values from tests/golden/batched64_oracle.txt (FP64 oracle on every "
                     "instance with chi <= 16, chi = 32 up to 127 qubits, chi = 64 at 27 qubits)"}
 
@@ -617,6 +694,9 @@ def run_ours(args, rank, world, local):
     batched = None
     if not args.no_batch and rank == 0:
         batched = batch_leg(tn, args)
+    serving_mix = None
+    if args.serve_mix > 0 and rank == 0:
+        serving_mix = serve_mix_leg(tn, args)
     fp32_line = None
     if args.fp32_steps > 0 and args.prec != "fp32":
         s3 = tn.TNState(n, edges, cols, chi=chi, prec="fp32", stream=stream, solve=args.solve)
@@ -661,7 +741,7 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "z_mean": float(np.mean(z)),
         "fp32_path": fp32_line,
-        "serving": serving, "batched": batched,
+        "serving": serving, "batched": batched, "serving_mix": serving_mix,
     }
     if fp32_line:
         fp32_line["mixed_over_fp32"] = round(value / world / fp32_line["value"], 3)

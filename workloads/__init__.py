@@ -81,3 +81,14 @@ def serving_jobs(n=2000, rate=200.0, seed=7):
     steps = r.integers(5, 21, size=n)
     return [(float(t[i]), int(sizes[i]), int(chis[i]), float(thetas[i]), int(steps[i]))
             for i in range(n)]
+
+
+def serving_oracle_sample(n_jobs=200, frac=0.02, seed=11):
+    """Indices of the seeded sample of the first `n_jobs` serving jobs that the
+    FP64 oracle checks: frac * n_jobs jobs (at least 1) drawn without
+    replacement among those with at most 127 qubits and chi at most 64."""
+    jobs = serving_jobs(n=2000)[:n_jobs]
+    elig = [i for i, j in enumerate(jobs) if j[1] <= 127 and j[2] <= 64]
+    k = max(1, int(round(frac * n_jobs)))
+    return sorted(int(i) for i in rng(seed).choice(elig, size=min(k, len(elig)), replace=False))
+
