@@ -411,8 +411,12 @@ tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats
  * e's first endpoint, ket x bra; columns: on its second); BP takes E as rank
  * one, and *error = 1 - sqrt(s_1^2 / sum_i s_i^2) over E's singular values s.
  * Exact contraction is exponential in the loops' size: meant for small
- * patches (a few heavy hexagons at small chi).  Host FP64 after the device
- * gauge; each bond keeps only the support of its lambda.
+ * patches (a few heavy hexagons at small chi).  FP64 on the device after the
+ * device gauge (double-layer tensors, pairwise contractions as complex GEMMs
+ * in a greedy order planned on the host from the shapes, and the eigenvalues
+ * of E^H E by a parallel Jacobi); each bond keeps only the support of its
+ * lambda.  Device memory of the contraction is allocated stream-ordered on
+ * the handle's stream and released before the call returns.
  *   sv_out       optional (may be NULL): the singular values of E in
  *                decreasing order, up to sv_capacity of them;
  *   n_sv         optional: their number (the squared support of lambda_e).

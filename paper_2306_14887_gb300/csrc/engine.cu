@@ -2320,6 +2320,24 @@ tn_status tn_get_gamma(tn_handle* h, int32_t v, float* host_out, size_t n_floats
   return TN_OK;
 }
 
+}  // extern "C"
+
+namespace tnbp {
+// Device view of the Vidal-gauge site tensor of v from the last tn_vidal_gauge
+// call (planar: the real plane [p][legs], then the imaginary plane), its
+// length chi^d and the handle's stream.
+tn_status gamma_view(tn_handle* h, int v, const float** ptr, int64_t* len, cudaStream_t* stream) {
+  if (!h->gamma) { set_error("tn_vidal_gauge has not run on this handle"); return TN_EINVAL; }
+  if (v < 0 || v >= h->g.n) { set_error("vertex out of range"); return TN_EINVAL; }
+  *ptr = h->gamma + h->t_off[v];
+  *len = h->t_len[v];
+  *stream = h->stream;
+  return TN_OK;
+}
+}  // namespace tnbp
+
+extern "C" {
+
 tn_status tn_truncation_solve(const float* gram, float* dmat, double* s_out, int32_t n_edges,
                               int32_t chi, int32_t sign, double svd_cutoff, void* cuda_stream) {
   return tn_truncation_solve_ex(gram, dmat, s_out, n_edges, chi, sign, svd_cutoff, TN_SOLVE_FP64,
