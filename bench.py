@@ -75,6 +75,9 @@ def parse():
                    help="jobs of the serving leg (0: skip)")
     p.add_argument("--serve-mix", type=int, default=0,
                    help="jobs of the full-mix serving leg (all sizes and chi; 0: skip)")
+    p.add_argument("--solve-bench", default="",
+                   help="only time the standalone truncation solves named here (comma-separated, "
+                        "e.g. refined,shared) on one layer-sized batch, and exit")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched 64-instance leg")
     p.add_argument("--batch-prec", default="tf32,tf32x3",
@@ -811,9 +814,53 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def solve_bench(args):
+    """The standalone truncation solve on one layer-sized batch: 51 edges at
+    chi = 64 (degree-3-like rows: 256 per open environment), seeded complex
+    Gaussian environment-weighted site matrices X with spectra decaying as
+    exp(-0.05 k), their open-p Gram matrices N_p = X_p^T conj(X_p) as the
+    inputs.  Prints one JSON line with the time per call of each solve."""
+    import torch
+    import paper_2306_14887_gb300 as tn
+    from paper_2306_14887_gb300 import build
+    build.build()
+    chi, ne, rows = 64, 51, 256
+    r = np.random.default_rng(5)
+    gram = np.zeros((ne, 2, 2, 2, chi, chi), dtype=np.float32)
+    for k in range(ne):
+        for side in range(2):
+            x = r.standard_normal((2, rows, chi)) + 1j * r.standard_normal((2, rows, chi))
+            x *= np.exp(-0.05 * np.arange(chi))[None, None, :]
+            for p in range(2):
+                n_p = x[p].T @ x[p].conj()
+                gram[k, side, p, 0], gram[k, side, p, 1] = n_p.real, n_p.imag
+    g = torch.from_numpy(gram.reshape(-1)).cuda()
+    d = torch.zeros_like(g)
+    sv = torch.zeros(ne * chi, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {"leg": "standalone truncation solve, %d edges, chi %d" % (ne, chi)}
+    for solve in args.solve_bench.split(","):
+        for _ in range(max(args.warmup, 1)):
+            tn.truncation_solve(g.data_ptr(), d.data_ptr(), sv.data_ptr(), ne, chi, 1,
+                                stream=st.cuda_stream, solve=solve)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            tn.truncation_solve(g.data_ptr(), d.data_ptr(), sv.data_ptr(), ne, chi, 1,
+                                stream=st.cuda_stream, solve=solve)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[solve + "_ms_per_call"] = round(e0.elapsed_time(e1) / args.steps, 4)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.solve_bench:
+        if rank == 0:
+            solve_bench(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
