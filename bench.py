@@ -75,6 +75,8 @@ def parse():
                    help="jobs of the serving leg (0: skip)")
     p.add_argument("--serve-mix", type=int, default=0,
                    help="jobs of the full-mix serving leg (all sizes and chi; 0: skip)")
+    p.add_argument("--serve-policy", default="shortest", choices=["fifo", "shortest"],
+                   help="admission order of the full-mix serving leg")
     p.add_argument("--solve-bench", default="",
                    help="only time the standalone truncation solves named here (comma-separated, "
                         "e.g. refined,shared) on one layer-sized batch, and exit")
@@ -205,8 +207,8 @@ def serve_mix_leg(tn, args):
     """The serving workload at its stated mix: the first --serve-mix jobs of the
     seeded Poisson stream (200 jobs/s; 27, 127, 433 and 1121 qubits; chi 16,
     32, 64 and 128; 5-20 steps) submitted at their arrival times to a server
-    with 8 slots admitting by HBM footprint.  Latency is arrival to result;
-    the <Z> error against the FP64 oracle on the seeded 2% sample of the jobs
+    with 8 slots admitting by HBM footprint in the --serve-policy order.
+    Latency is arrival to result; the <Z> error against the FP64 oracle on the seeded 2% sample of the jobs
     with at most 127 qubits and chi at most 64."""
     from workloads import serving_jobs
     n, edges, cols = eagle()
@@ -217,7 +219,7 @@ def serve_mix_leg(tn, args):
     gold = read_serving_golden()
     lat, steps_done, dz = [], 0, {}
     by_kind = {}
-    with tn.Server(slots=8) as srv:
+    with tn.Server(slots=8, policy=args.serve_policy) as srv:
         t0 = time.perf_counter()
         tickets = []
         for (arr, size, chi, theta, steps) in stream:
@@ -236,6 +238,7 @@ def serve_mix_leg(tn, args):
         st = srv.stats()
     lat = np.array(lat)
     return {"jobs": len(lat), "slots": 8, "arrival_rate_per_s": 200.0,
+            "policy": args.serve_policy,
             "p50_s": round(float(np.percentile(lat, 50)), 3),
             "p99_s": round(float(np.percentile(lat, 99)), 3),
             "p50_s_by_size": {k: round(float(np.percentile(v, 50)), 3) for k, v in by_kind.items()},

@@ -472,7 +472,16 @@ typedef struct {
   size_t hbm_budget;   /* bytes the resident jobs may hold; 0: 90% of free device memory */
   int32_t max_slots;   /* jobs resident and running at once, 1..64 */
   int32_t device;      /* CUDA device ordinal */
+  int32_t policy;      /* which queued job a free slot takes (TN_SERVE_*); 0: oldest first */
 } tn_server_config;
+
+/* Admission order of a server.  TN_SERVE_FIFO: the oldest queued job, once it
+ * fits the HBM budget (later jobs wait behind it).  TN_SERVE_SHORTEST: among
+ * the queued jobs that fit, the one with the least estimated work
+ * steps x (sum_v d_v chi^(d_v + 1) + 8 n_edges chi^3) (the BP message updates
+ * and the truncation solves), the oldest among equals. */
+#define TN_SERVE_FIFO 0
+#define TN_SERVE_SHORTEST 1
 
 typedef struct {
   tn_graph graph;      /* copied at submit */

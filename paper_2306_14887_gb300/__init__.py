@@ -86,7 +86,8 @@ class tn_pauli(C.Structure):
 
 
 class tn_server_config(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int32), ("device", C.c_int32)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int32), ("device", C.c_int32),
+                ("policy", C.c_int32)]
 
 
 class tn_job(C.Structure):
@@ -593,11 +594,16 @@ class Batch:
 class Server:
     """Continuous-batching job server on one device (see tn_server_* in tnbp.h)."""
 
-    def __init__(self, slots=4, hbm_budget=0, device=None):
+    POLICIES = {"fifo": 0, "shortest": 1}
+
+    def __init__(self, slots=4, hbm_budget=0, device=None, policy="fifo"):
+        """policy: "fifo" (oldest queued job first) or "shortest" (least
+        estimated work first among the jobs that fit)."""
         import torch
         cfg = tn_server_config()
         cfg.hbm_budget = int(hbm_budget)
         cfg.max_slots = int(slots)
+        cfg.policy = self.POLICIES[policy]
         cfg.device = int(torch.cuda.current_device() if device is None else device)
         h = C.c_void_p()
         _check(lib().tn_server_create(C.byref(cfg), C.byref(h)))

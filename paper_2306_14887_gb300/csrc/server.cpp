@@ -5,15 +5,17 @@
 // and its kernels overlap theirs on the device).
 //
 // Design: max_slots host threads ("slots"), each with its own non-blocking CUDA
-// stream.  A slot takes the oldest queued job once the sum of the resident
-// jobs' footprints (tn_footprint_estimate) plus the job's own stays within the
-// budget, creates the job's handle on its stream with stream-ordered
+// stream.  A slot takes a queued job once the sum of the resident jobs'
+// footprints (tn_footprint_estimate) plus the job's own stays within the
+// budget: the oldest (TN_SERVE_FIFO) or the one with the least estimated work
+// among those that fit (TN_SERVE_SHORTEST); it creates the job's handle on its stream with stream-ordered
 // allocation (cudaMallocAsync / cudaFreeAsync, so that freeing never
 // synchronises the device), runs every step, reads <Z_v> for all vertices and
 // destroys the handle.  Jobs never share device memory or streams, and every
 // kernel of the library is deterministic (fixed reduction orders), so a job's
 // result is the same whether it runs alone or in a mix.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -45,6 +47,7 @@ struct Job {
   double theta = 0.0;
   int32_t steps = 0;
   size_t footprint = 0;
+  double work = 0.0;  // estimated work (TN_SERVE_SHORTEST)
   Clock::time_point t_submit, t_admit, t_done;
   tn_status status = TN_EAGAIN;
   int32_t steps_done = 0;
@@ -86,6 +89,18 @@ struct tn_server {
   std::vector<std::thread> slots;
 
   void run_slot();
+  // the queued job a free slot takes next under the policy (queue.end(): none fits)
+  std::deque<std::shared_ptr<Job>>::iterator pick() {
+    if (queue.empty()) return queue.end();
+    if (cfg.policy != TN_SERVE_SHORTEST)
+      return st.used_bytes + queue.front()->footprint <= budget ? queue.begin() : queue.end();
+    auto best = queue.end();
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      if (st.used_bytes + (*it)->footprint > budget) continue;
+      if (best == queue.end() || (*it)->work < (*best)->work) best = it;
+    }
+    return best;
+  }
 };
 
 void tn_server::run_slot() {
@@ -97,12 +112,11 @@ void tn_server::run_slot() {
     std::shared_ptr<Job> job;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] {
-        return stopping || (!queue.empty() && st.used_bytes + queue.front()->footprint <= budget);
-      });
+      cv.wait(lk, [&] { return stopping || pick() != queue.end(); });
       if (stopping) break;
-      job = queue.front();
-      queue.pop_front();
+      const auto it = pick();
+      job = *it;
+      queue.erase(it);
       st.used_bytes += job->footprint;
       st.resident++;
       if (st.used_bytes > st.peak_bytes) st.peak_bytes = st.used_bytes;
@@ -171,6 +185,7 @@ tn_status tn_server_create(const tn_server_config* cfg, tn_server** out) {
   if (!cfg || !out) return TN_EINVAL;
   *out = nullptr;
   if (cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->device < 0) return TN_EINVAL;
+  if (cfg->policy != TN_SERVE_FIFO && cfg->policy != TN_SERVE_SHORTEST) return TN_EINVAL;
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || cfg->device >= count) {
     cudaGetLastError();
@@ -214,6 +229,17 @@ tn_status tn_server_submit(tn_server* s, const tn_job* job, uint64_t* ticket) {
   j->theta = job->theta_h;
   j->steps = job->steps;
   j->footprint = fp;
+  {
+    // estimated work: BP message updates (chi^(d+1) per site and leg) and the
+    // truncation solves (chi^3 per edge), per step
+    std::vector<int> deg(j->n, 0);
+    for (size_t k = 0; k < j->edges.size(); ++k)
+      if (j->edges[k] >= 0 && j->edges[k] < j->n) deg[j->edges[k]]++;
+    const double x = job->cfg.chi;
+    double w = 8.0 * (double)job->graph.n_edges * x * x * x;
+    for (int d : deg) w += d * std::pow(x, d + 1);
+    j->work = w * std::max(1, job->steps);
+  }
   if (job->n_ops < 0 || (job->n_ops > 0 && !job->ops) ||
       (job->n_ops > 0 && job->ops_method != 0 && job->ops_method != 1))
     return TN_EINVAL;

@@ -77,6 +77,31 @@ def test_admission_by_footprint(tnlib):
     assert stats["peak_bytes"] <= int(1.5 * fp)
 
 
+def test_shortest_policy_admits_small_jobs_first(tnlib):
+    """One slot busy with a first job; then a large job and two small ones
+    queue.  Under TN_SERVE_SHORTEST the small ones are admitted before the
+    large one (oldest first would take the large one); results are those of
+    the jobs alone."""
+    g, p = OG.eagle127(), OG.falcon27_patch()
+    with tnlib.Server(slots=1, policy="shortest") as srv:
+        first = srv.submit(g.n, g.edges, g.colours, 16, 0.5, 3, prec="tf32")
+        big = srv.submit(g.n, g.edges, g.colours, 32, 0.6, 4, prec="tf32")
+        small = [srv.submit(p.n, p.edges, p.colours, 8, 0.3 + 0.1 * i, 2, prec="tf32")
+                 for i in range(2)]
+        srv.wait(first)
+        zb, ib = srv.wait(big)
+        outs = [srv.wait(t) for t in small]
+    for (z, info), i in zip(outs, range(2)):
+        assert info["queue_s"] < ib["queue_s"]
+        assert np.abs(z - _alone(tnlib, p, 8, 0.3 + 0.1 * i, 2, "tf32")).max() <= 1e-12
+    assert np.abs(zb - _alone(tnlib, g, 32, 0.6, 4, "tf32")).max() <= 1e-12
+
+
+def test_unknown_policy_is_refused(tnlib):
+    with pytest.raises(KeyError):
+        tnlib.Server(slots=1, policy="random")
+
+
 def test_job_over_budget_is_refused(tnlib):
     g = OG.eagle127()
     with tnlib.Server(slots=1, hbm_budget=1 << 20) as srv:
