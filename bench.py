@@ -80,6 +80,9 @@ def parse():
     p.add_argument("--solve-bench", default="",
                    help="only time the standalone truncation solves named here (comma-separated, "
                         "e.g. refined,shared) on one layer-sized batch, and exit")
+    p.add_argument("--no-peaks", action="store_true",
+                   help="skip the torch.matmul rate measurements (the roofline then takes the "
+                        "peaks file and the nominal ratios), e.g. under a profiler")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched 64-instance leg")
     p.add_argument("--batch-prec", default="tf32,tf32x3",
@@ -628,7 +631,7 @@ def run_ours(args, rank, world, local):
     presteps = args.presteps if args.presteps is not None else int(np.log2(max(chi, 1))) + 1
     theta = theta_for(rank, args)
     n, edges, cols = eagle()
-    mp = measure_peaks()
+    mp = {} if args.no_peaks else measure_peaks()
     stream = torch.cuda.Stream()
     s = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream, solve=args.solve,
                      kernels=args.kernels)
@@ -694,6 +697,9 @@ def run_ours(args, rank, world, local):
     nbd = {d: int(sum(1 for v in range(n) if int(np.sum(edges == v)) == d)) for d in (1, 2, 3)}
     rl = roofline(prof, args.prec, chi, bp_iters, nbd, solve_kind(args.solve, chi), mp)
     rl["share_of_timed"] = round(prof[rl["kernel"]]["ms"] / ms, 4)
+    if not mp:
+        rl["peak_source"] = ("not measured in this run (--no-peaks): the peaks file or the "
+                             "nominal figure in its place")
     serving = None
     if args.serve_jobs > 0 and rank == 0:
         serving = serve_leg(tn, args)

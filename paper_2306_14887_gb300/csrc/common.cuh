@@ -228,7 +228,6 @@ struct RefineLayout {
   int64_t L;      // [2][chi][chi] complex: FP64 Cholesky factors of the G_v blocks
   int64_t U;      // [n][n] complex: starting basis, column m at U + 2 n m
   int64_t U1;     // [chi][n] complex: refined kept columns
-  int64_t G;      // [n][n] complex: conj(G_w) in FP64
   int64_t lam0;   // [n]: sigma^2 of the starting basis (decreasing)
   int64_t lam1;   // [chi]: refined eigenvalues of the kept columns
   int64_t misc;   // [4]: sum of all sigma^2 of the start, FP32 sweeps
@@ -242,8 +241,7 @@ __host__ __device__ inline RefineLayout refine_layout(int chi) {
   l.L = 0;
   l.U = l.L + 4 * (int64_t)chi * chi;
   l.U1 = l.U + 2 * n * n;
-  l.G = l.U1 + 2 * n * chi;
-  l.lam0 = l.G + 2 * n * n;
+  l.lam0 = l.U1 + 2 * n * chi;
   l.lam1 = l.lam0 + n;
   l.misc = l.lam1 + chi;
   l.ints = l.misc + 4;

@@ -1026,12 +1026,13 @@ tn_status gate_layer(tn_handle* h, int li, int sign) {
       const double n = 2.0 * h->chi, x = h->chi;
       // FP32 phase (Jacobi sweeps: about 7 of n^2/2 pairs x 16 n real flops)
       prof_end(h, pi, 7.0 * n * n / 2 * 16.0 * n * a.n_edges, 0.0);
-      // FP64 phase: Newton step (Y, P: chi^3 each; Z, S, R and the update:
-      // n^2 chi each) and the leg matrices (2 chi^3), 8 real flops per cMAC
+      // FP64 phase: Newton step (Y, P: chi^3 each; Z through the two open-q
+      // environments: n^2 chi / 2; S, R and the update: n^2 chi each) and the
+      // leg matrices (2 chi^3), 8 real flops per cMAC
       const int pr = prof_begin(h, P_REFINE);
       TN_CUDA_TRY(launch_solve_refined_newton(a, h->stream));
-      prof_end(h, pr, 8.0 * (4.0 * x * x * x + 4.0 * n * n * x) * a.n_edges,
-               16.0 * (3.0 * n * n + n * x) * a.n_edges);
+      prof_end(h, pr, 8.0 * (4.0 * x * x * x + 3.5 * n * n * x) * a.n_edges,
+               (16.0 * (2.0 * n * n + n * x) + 4.0 * n * n) * a.n_edges);
       h->stats.kernel_launches += 3;
     } else if (kind == TN_SOLVE_SHARED) {
       a.max_sweeps = 20;

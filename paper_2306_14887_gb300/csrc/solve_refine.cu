@@ -222,28 +222,6 @@ __global__ void __launch_bounds__(kThreads) chol64_kernel(SolveArgs a) {
       L[idx] = A[i * ld + j];
     }
   if (threadIdx.x == 0) ints[2 * chi + b] = rank_s;
-  // rows (k = b, e) of conj(G_w) in FP64 (exact from the FP32 inputs):
-  // conj(G_w)[(k,e), (k',e')] = N_0 + N_1 for k = k', +s i (N_0 - N_1) for
-  // (0, 1) and -s i (N_0 - N_1) for (1, 0), N_q = N_q^w[e][e']
-  const float* gw = a.gram + (int64_t)edge * 8 * c2 + 4 * c2;
-  cd* G = reinterpret_cast<cd*>(base + lay.G);
-  const int n = 2 * chi;
-  const double f = (b == 0) ? (double)a.sign : -(double)a.sign;
-  for (int idx = threadIdx.x; idx < chi * n; idx += blockDim.x) {
-    const int e = idx / n, r = idx - e * n;
-    const int k2 = r / chi, e2 = r - k2 * chi;
-    const int64_t o = (int64_t)e * chi + e2;
-    const cd n0 = {(double)gw[o], (double)gw[c2 + o]};
-    const cd n1 = {(double)gw[2 * c2 + o], (double)gw[3 * c2 + o]};
-    cd val;
-    if (k2 == b) {
-      val = cadd(n0, n1);
-    } else {
-      const cd d = csub(n0, n1);
-      val = {-f * d.y, f * d.x};
-    }
-    G[(int64_t)(b * chi + e) * n + r] = val;
-  }
 }
 
 // ------------------------------------------------------------ refinement
@@ -257,7 +235,7 @@ struct EdgeView {
   const double* lam0;  // [n]
   double* lam1;        // [chi]
   const double* misc;  // [0] sum of sigma^2 of the start
-  const cd* G;         // [n][n] conj(G_w)
+  const float* gw;     // [q][re|im][chi][chi] the open-q environments N_q^w (FP32 inputs)
 };
 
 __device__ EdgeView edge_view(const SolveArgs& a, int edge) {
@@ -276,7 +254,7 @@ __device__ EdgeView edge_view(const SolveArgs& a, int edge) {
   v.lam0 = base + lay.lam0;
   v.lam1 = base + lay.lam1;
   v.misc = base + lay.misc;
-  v.G = reinterpret_cast<const cd*>(base + lay.G);
+  v.gw = a.gram + (int64_t)edge * 8 * (int64_t)a.chi * a.chi + 4 * (int64_t)a.chi * a.chi;
   return v;
 }
 
@@ -328,9 +306,10 @@ __device__ void rows8(int nrows, int cw, const cd* B, int ldb, RF range, AF arow
 
 // One Newton step for the kept columns [j0, j1) of one edge.  Shared-memory
 // buffers (column-major, column j at j * n): Uc (the start's columns), B1
-// (Y = R_v^H U_c, then P = H U_c), B2 (Z = conj(G_w) Y, then S, then the
-// update coefficients), B3 (R); lamc the columns' Rayleigh quotients (negated
-// start eigenvalue for tail columns), lamf the final eigenvalues.
+// (Y = R_v^H U_c, then P = H U_c), B2 (T = N_q^w Y'_q, then S, then the
+// update coefficients), B3 (Y'_q, then Z = conj(G_w) Y, then R); lamc the
+// columns' Rayleigh quotients (negated start eigenvalue for tail columns),
+// lamf the final eigenvalues.
 __device__ void refine_chunk(const SolveArgs& a, const EdgeView& v, int j0, int j1, cd* Uc, cd* B1,
                              cd* B2, cd* B3, double* lamc, double* lamf) {
   const int chi = v.chi, n = v.n, A = v.act;
@@ -360,15 +339,46 @@ __device__ void refine_chunk(const SolveArgs& a, const EdgeView& v, int j0, int 
         B1[j * n + k * chi + v.perm[k * chi + s]] = val;
       });
   __syncthreads();
-  // Z = conj(G_w) Y
+  // Z = conj(G_w) Y through the rank-one phase structure of G_w: with the
+  // global phase of b(q) chosen so that b_q(q) = 1 and b_k(q) = -i s (k != q),
+  // conj(G_w) = sum_q c(q) c(q)^H (x) N_q^w, c(0) = (1, -i s), c(1) = (-i s, 1),
+  // so Z = sum_q c(q) (x) N_q^w Y'_q with Y'_q = c(q)^H Y:
+  //   Y'_0 = Y_0 + i s Y_1,  Y'_1 = i s Y_0 + Y_1      (into B3)
+  //   T_q = N_q^w Y'_q                                  (into B2; two chi x chi products)
+  //   Z_0 = T_0 - i s T_1,   Z_1 = -i s T_0 + T_1       (into B3)
+  // The factors +-i s are exact, so this is conj(G_w) Y with half the products.
+  const double sg = (double)a.sign;
+  for (int idx = tid; idx < cw * n; idx += blockDim.x) {
+    const int j = idx / n, i = idx - j * n;
+    const int q = i / chi, e = i - q * chi;
+    const cd y0 = B1[j * n + e], y1 = B1[j * n + chi + e];
+    const cd other = q == 0 ? y1 : y0;             // the term multiplied by i s
+    const cd mine = q == 0 ? y0 : y1;
+    B3[j * n + i] = {mine.x - sg * other.y, mine.y + sg * other.x};
+  }
+  __syncthreads();
   rows8(
-      n, cw, B1, n, [&](int, int& lo, int& hi) { lo = 0; hi = n; },
-      [&](int i, int r) { return v.G[(int64_t)i * n + r]; }, [&](int, int r) { return r; },
+      n, cw, B3, n, [&](int, int& lo, int& hi) { lo = 0; hi = chi; },
+      [&](int i, int r) {
+        const int q = i / chi, e = i - q * chi;
+        const int64_t o = (int64_t)q * 2 * c2 + (int64_t)e * chi + r;
+        return cd{(double)v.gw[o], (double)v.gw[c2 + o]};
+      },
+      [&](int i, int r) { return (i / chi) * chi + r; },
       [&](int i, int j, cd val) { B2[j * n + i] = val; });
+  __syncthreads();
+  for (int idx = tid; idx < cw * n; idx += blockDim.x) {
+    const int j = idx / n, i = idx - j * n;
+    const int k = i / chi, e = i - k * chi;
+    const cd t0 = B2[j * n + e], t1 = B2[j * n + chi + e];
+    const cd other = k == 0 ? t1 : t0;             // the term multiplied by -i s
+    const cd mine = k == 0 ? t0 : t1;
+    B3[j * n + i] = {mine.x + sg * other.y, mine.y - sg * other.x};
+  }
   __syncthreads();
   // P = R_v Z: P[(b, t)] = sum_{s >= t} conj(L_b[s][t]) Z[(b, perm_b[s])], zero for t >= rank_b
   rows8(
-      n, cw, B2, n,
+      n, cw, B3, n,
       [&](int i, int& lo, int& hi) {
         const int b = i / chi, t = i - b * chi;
         lo = t;
@@ -738,7 +748,7 @@ cudaError_t launch_solve_refined_basis(const SolveArgs& a, cudaStream_t st) {
   if (a.n_edges <= 0) return cudaSuccess;
   if (!solve_refined_supported(a.chi)) return cudaErrorInvalidValue;
   const int chi = a.chi;
-  // 1. FP64 Cholesky of the v-side Gram blocks, conj(G_w) in FP64
+  // 1. FP64 Cholesky of the v-side Gram blocks
   const size_t sm_chol = chi <= kSmemChi ? sizeof(cd) * (size_t)chi * (chi + 1) : 0;
   cudaError_t e = refine_prepare();
   if (e != cudaSuccess) return e;
