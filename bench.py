@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--no-peaks", action="store_true",
                    help="skip the torch.matmul rate measurements (the roofline then takes the "
                         "peaks file and the nominal ratios), e.g. under a profiler")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the heuristic split-K counts of the sweep launches")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched 64-instance leg")
     p.add_argument("--batch-prec", default="tf32,tf32x3",
@@ -636,6 +638,17 @@ def run_ours(args, rank, world, local):
     s = tn.TNState(n, edges, cols, chi=chi, prec=args.prec, stream=stream, solve=args.solve,
                      kernels=args.kernels)
     s.apply_floquet(theta, presteps)
+    tune = None
+    if not args.no_autotune:
+        # split-K counts of the sweep launches timed on this state (untimed setup)
+        table = s.autotune(reps=5)
+        rows = [ln.split() for ln in table.strip().splitlines() if ln.strip()]
+        tune = {"rows": len(rows),
+                "split_counts": {k: sum(1 for r in rows if r[7] == k)
+                                 for k in sorted({r[7] for r in rows}, key=int)},
+                "note": "tn_autotune on the bench state after the untimed steps: per sweep "
+                        "launch with a split-K count, the fastest power of two (kept only "
+                        "when 3% faster than the heuristic's)"}
     for _ in range(args.warmup):
         s.apply_floquet(theta, 1)
     clk = ClockSampler(local)
@@ -743,6 +756,7 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (initial state |0..0>, theta_h from the uniform [0, pi/2] grid)",
         "config": workload_config(args, world),
         "gpu_launches": int(launches),
+        "autotune": tune,
         "tma_stream_launches": int(tma_launches),
         "bp_sweeps_per_step": round(bp_iters / args.steps, 2),
         "discarded_weight_max": disc,

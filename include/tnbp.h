@@ -252,6 +252,42 @@ tn_status tn_bp_converge(tn_handle* h, double tol, int32_t max_iters,
 tn_status tn_bp_components(tn_handle* h, int32_t* comp_of_vertex, int32_t* sweeps_out,
                            double* residual_out, int32_t cap, int32_t* n_comp_out);
 
+/*
+ * tn_autotune — choose the split-K count of every BP-sweep launch that has one
+ * (the TMA split-K closes, the tensor-core tile GEMMs, the CUDA-core GEMMs;
+ * not the fused chain kernels, whose tiles are fixed) by timing each valid
+ * power-of-two count from 1 to 64 on the handle's own state and buffers:
+ * one warm-up launch, then `reps` launches timed with CUDA events on the
+ * handle's stream.  A count replaces the current one only when it is at least
+ * 3% faster.  The launches the captured sweep runs on its side stream keep a
+ * single split.  The sweep launches read the state and write only scratch
+ * and the raw messages, so the state is unchanged; the next BP iteration
+ * captures its loop again with the new counts, and its results may differ
+ * from the untuned ones in the last FP32 bits (the order of the partial
+ * sums).  Per (chi, degree, precision) the launch shapes fix the key of a
+ * table row, so a table tuned on one handle applies to any handle of the same
+ * chi, precision and graph shape.
+ *   reps       timed launches per candidate, >= 1
+ *   table_out  optional (may be NULL): the table as text, one row per tuned
+ *              launch: "kind M N K outer inner prec splits us_per_launch\n"
+ *              (kind: close, tile or simt), truncated to table_cap - 1 bytes
+ *              and NUL-terminated;
+ *   table_len  optional: the table's full length in bytes.
+ * Errors: TN_EINVAL (null handle, reps < 1), TN_ECUDA.
+ */
+tn_status tn_autotune(tn_handle* h, int32_t reps, char* table_out, size_t table_cap,
+                      size_t* table_len);
+
+/*
+ * tn_autotune_apply — set the split counts of a table written by tn_autotune
+ * (on this or another handle): every sweep launch whose key (kind, M, N, K,
+ * outer, inner, prec) has a row takes that row's count if it is valid for
+ * this handle (its partials fit); other launches keep theirs.  table: a
+ * NUL-terminated text, caller-owned.  n_applied (may be NULL): rows applied.
+ * Errors: TN_EINVAL (null argument).
+ */
+tn_status tn_autotune_apply(tn_handle* h, const char* table, int32_t* n_applied);
+
 /* A Pauli string sign * prod_j P_{sites[j]}, P in {'X','Y','Z'}; sites distinct. */
 typedef struct {
   int32_t weight;

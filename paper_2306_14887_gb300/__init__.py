@@ -36,7 +36,8 @@ EXPORTS = ["tn_create", "tn_destroy", "tn_apply_floquet", "tn_apply_clifford_dag
            "tn_server_poll_ex", "tn_server_wait_ex",
            "tn_bond_spectrum", "tn_entanglement_entropy", "tn_state_size", "tn_save_state",
            "tn_load_state", "tn_chi_extrapolate", "tn_vidal_gauge", "tn_get_gamma",
-           "tn_bp_error", "tn_graph_info", "tn_selftest_bounded_wait", "tn_bp_components"]
+           "tn_bp_error", "tn_graph_info", "tn_selftest_bounded_wait", "tn_bp_components",
+           "tn_autotune", "tn_autotune_apply"]
 
 
 class TNError(RuntimeError):
@@ -125,6 +126,8 @@ def lib():
         L.tn_apply_floquet.argtypes = [vp, C.c_double, i32]
         L.tn_apply_clifford_dagger.argtypes = [vp, i32]
         L.tn_bp_converge.argtypes = [vp, C.c_double, i32, C.POINTER(i32), dp]
+        L.tn_autotune.argtypes = [vp, i32, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.tn_autotune_apply.argtypes = [vp, C.c_char_p, C.POINTER(i32)]
         L.tn_bp_components.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), dp, i32, C.POINTER(i32)]
         L.tn_expect.argtypes = [vp, C.POINTER(tn_pauli), i32, i32, dp]
         L.tn_expect_z_all.argtypes = [vp, dp]
@@ -356,6 +359,34 @@ class TNState:
         if s not in (TN_OK, -3):
             _check(s)
         return it.value, res.value, s
+
+    def autotune(self, reps=5):
+        """Time the split-K counts of the BP-sweep launches (tn_autotune) and
+        keep the fastest; returns the table as text."""
+        n = C.c_size_t()
+        buf = C.create_string_buffer(1 << 20)
+        _check(lib().tn_autotune(self._h, int(reps), buf, len(buf), C.byref(n)))
+        if n.value >= len(buf):
+            raise RuntimeError("autotune table longer than its buffer")
+        return buf.value.decode()
+
+    def apply_tuning(self, table):
+        """Apply a table from autotune (this or another handle); returns the
+        number of rows applied."""
+        k = C.c_int32()
+        _check(lib().tn_autotune_apply(self._h, table.encode(), C.byref(k)))
+        return k.value
+
+    def save_tuning(self, path, reps=5):
+        """Autotune and write the table to a text file."""
+        table = self.autotune(reps)
+        with open(path, "w") as f:
+            f.write(table)
+        return table
+
+    def load_tuning(self, path):
+        with open(path) as f:
+            return self.apply_tuning(f.read())
 
     def bp_components(self):
         """(comp_of_vertex, sweeps, residuals) of the last BP iteration, per

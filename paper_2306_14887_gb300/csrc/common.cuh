@@ -81,15 +81,20 @@ __host__ __device__ __forceinline__ int64_t row_off3(int m, int M2, int M3, int6
 // CUDA-core complex GEMM (kernels.cu); with part != nullptr (part_cap floats) a
 // launch whose grid is under one wave is split over K into partials (cgemm_plan
 // gives the count and the partial floats) and summed by the fixed-order reduce.
-int cgemm_plan(const GemmDesc& d, size_t* part_floats);
+// force_splits > 0 replaces the heuristic split count (the autotuner's
+// choice); a count whose partials would not fit part_cap falls back to one.
+int cgemm_plan(const GemmDesc& d, size_t* part_floats, int force_splits = 0);
 cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s, float* part = nullptr,
-                         size_t part_cap = 0, int* n_kernels = nullptr);
+                         size_t part_cap = 0, int* n_kernels = nullptr, int force_splits = 0);
 // Tensor-core version (tc_gemm.cu) for TN_TF32 / TN_BF16 descriptors.  part:
-// scratch for K-split partial products (tc_plan gives the size); err: bit 1 is
-// set when a device-side wait gave up.
-bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats);
+// scratch for K-split partial products (tc_plan gives the size, part_cap the
+// floats the caller holds: a plan that needs more is refused); err: bit 1 is
+// set when a device-side wait gave up.  force_splits as for cgemm_plan.
+bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats,
+             int force_splits = 0);
 cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t s,
-                            int* n_kernels = nullptr);
+                            int* n_kernels = nullptr, int force_splits = 0,
+                            size_t part_cap = (size_t)-1);
 // Persistent TMA-fed kernel for mode products (tc_stream.cu): one A and one B
 // tensor map per batch entry, encoded on the host when a plan is uploaded.
 struct TcStreamPlan {

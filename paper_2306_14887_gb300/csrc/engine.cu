@@ -50,6 +50,7 @@ struct HostLaunch {
   TcStreamPlan sp;         // maps set: the launch runs in a TMA kernel
   bool fuse_next = false;  // the next launch contracts this one's output (chain stages)
   bool skip = false;       // carried out by the previous launch's fused kernel
+  int tuned = 0;           // split-K count chosen by tn_autotune (0: the heuristic)
 };
 
 struct Plan {
@@ -487,10 +488,11 @@ tn_status run_plan(tn_handle* h, const Plan& P, int cls, size_t begin = 0,
       TN_CUDA_TRY(launch_tc_stream(L.d, L.sp, h->flags, stream));
       h->stats.tma_launches++;
     } else if (use_tensor_cores(h) && !tiny) {
-      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, stream, &nk));
+      TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, stream, &nk, L.tuned, h->part_floats));
     } else {
       // a tiny-grid launch on the main stream may split K into the partial buffer
-      TN_CUDA_TRY(launch_cgemm(L.d, stream, on_side ? nullptr : h->part, h->part_floats, &nk));
+      TN_CUDA_TRY(launch_cgemm(L.d, stream, on_side ? nullptr : h->part, h->part_floats, &nk,
+                               L.tuned));
     }
     if (pi >= 0) {
       double f, b;
@@ -516,11 +518,11 @@ bool side_safe(const tn_handle* h, const Plan& P, size_t begin) {
     if (use_tensor_cores(h) && !(macs < 262144.0)) {
       int q = 0, sp = 1;
       size_t pf = 0;
-      tc_plan(L.d, &q, &sp, &pf);
+      tc_plan(L.d, &q, &sp, &pf, L.tuned);
       if (sp > 1) return false;
     } else {
       size_t pf = 0;
-      if (cgemm_plan(L.d, &pf) > 1) return false;
+      if (cgemm_plan(L.d, &pf, L.tuned) > 1) return false;
     }
   }
   return true;
@@ -1200,6 +1202,76 @@ void sweep_work(tn_handle* h) {
   }
 }
 
+// ---------------------------------------------------------------- autotuner
+// The split-K count of each sweep launch that has one: the TMA closes (kind 1),
+// the tensor-core tile GEMM and the CUDA-core GEMM.  Key of a launch: its
+// kind, M, N, K, entries (outer x inner) and precision.
+enum TuneKind { TUNE_NONE = 0, TUNE_CLOSE = 1, TUNE_TILE = 2, TUNE_SIMT = 3 };
+const char* kTuneNames[] = {"none", "close", "tile", "simt"};
+
+int tune_kind(const tn_handle* h, const HostLaunch& L) {
+  if (L.skip) return TUNE_NONE;
+  if (L.sp.maps) return L.sp.kind == 1 ? TUNE_CLOSE : TUNE_NONE;
+  const double macs = (double)L.d.n_outer * L.d.n_inner * L.d.M * L.d.N * L.d.K1 * L.d.K2;
+  return (use_tensor_cores(h) && !(macs < 262144.0)) ? TUNE_TILE : TUNE_SIMT;
+}
+
+// The split count a launch runs with now, and whether `s` is a valid count
+// for it (its partials fit the handle's buffer, every split holds K work).
+int current_splits(const tn_handle* h, const HostLaunch& L, int kind) {
+  size_t pf = 0;
+  if (kind == TUNE_CLOSE) return L.sp.splits;
+  if (kind == TUNE_TILE) {
+    int q, sp;
+    tc_plan(L.d, &q, &sp, &pf, L.tuned);
+    return sp;
+  }
+  return cgemm_plan(L.d, &pf, L.tuned);
+}
+
+bool splits_valid(const tn_handle* h, const HostLaunch& L, int kind, int s) {
+  const size_t entries = (size_t)L.d.n_outer * L.d.n_inner;
+  const size_t pf = s > 1 ? (size_t)s * entries * 2 * L.d.M * L.d.N : 0;
+  if (pf > h->part_floats) return false;
+  if (kind == TUNE_CLOSE) {
+    const int chunks = L.d.K1 * L.d.K2 / 32;
+    const int per = (chunks + s - 1) / s;
+    return s >= 1 && s <= 64 && (chunks + per - 1) / per == s;  // no empty split
+  }
+  if (kind == TUNE_TILE) {
+    int q, sp;
+    size_t p2;
+    tc_plan(L.d, &q, &sp, &p2, s);
+    return sp == s;
+  }
+  size_t p2;
+  return cgemm_plan(L.d, &p2, s) == s;
+}
+
+void set_splits(HostLaunch& L, int kind, int s) {
+  if (kind == TUNE_CLOSE) L.sp.splits = s;
+  else L.tuned = s;
+}
+
+std::string tune_key(const HostLaunch& L, int kind) {
+  char buf[160];
+  snprintf(buf, sizeof(buf), "%s %d %d %lld %d %d %d", kTuneNames[kind], L.d.M, L.d.N,
+           (long long)L.d.K1 * L.d.K2, L.d.n_outer, L.d.n_inner, L.d.prec);
+  return buf;
+}
+
+tn_status launch_one(tn_handle* h, const HostLaunch& L, int kind) {
+  int nk = 0;
+  if (kind == TUNE_CLOSE) {
+    TN_CUDA_TRY(launch_tc_close(L.d, L.sp, h->part, h->flags, h->stream));
+  } else if (kind == TUNE_TILE) {
+    TN_CUDA_TRY(launch_cgemm_tc(L.d, h->part, h->flags, h->stream, &nk, L.tuned, h->part_floats));
+  } else {
+    TN_CUDA_TRY(launch_cgemm(L.d, h->stream, h->part, h->part_floats, &nk, L.tuned));
+  }
+  return TN_OK;
+}
+
 tn_status bp_converge_impl(tn_handle* h, double tol, int max_iters, int* iters, double* res) {
   // Messages are stored in FP32: once the residual is down at the rounding
   // floor of the arithmetic it stops decreasing and only fluctuates.  Below
@@ -1733,6 +1805,116 @@ tn_status tn_bp_converge(tn_handle* h, double tol, int32_t max_iters, int32_t* i
   if (iters_out) *iters_out = it;
   if (residual_out) *residual_out = r;
   return st;
+}
+
+tn_status tn_autotune(tn_handle* h, int32_t reps, char* table_out, size_t table_cap,
+                      size_t* table_len) {
+  if (!h || reps < 1) { set_error("null handle or reps < 1"); return TN_EINVAL; }
+  tn_status st = ensure_ta(h);
+  if (st) return st;
+  st = ensure_mrt(h);
+  if (st) return st;
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const bool prof = h->prof_on;
+  h->prof_on = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    h->prof_on = prof;
+    set_error("cudaEventCreate failed");
+    return TN_ECUDA;
+  }
+  std::string table;
+  // the sweep's launches read the state and write only the sweep's scratch and
+  // raw messages, which the next sweep recomputes from the state
+  for (size_t li = 0; li < h->sweep.L.size(); ++li) {
+    HostLaunch& L = h->sweep.L[li];
+    const int kind = tune_kind(h, L);
+    // the launches the captured sweep may run on its side stream keep one
+    // split (partials live in the one buffer of the main stream)
+    if (kind == TUNE_NONE || (h->sweep_split > 0 && li >= h->sweep_split)) continue;
+    const int now = current_splits(h, L, kind);
+    // every valid power-of-two count, timed over `reps` launches after one
+    // warm-up launch; the fastest replaces the current count only when it is
+    // at least 3% faster (timing noise keeps the heuristic's choice)
+    int best = now, fastest = 0;
+    float now_ms = -1.f, fastest_ms = 0.f;
+    for (int sc = 1; sc <= 64 && !st; sc *= 2) {
+      if (!splits_valid(h, L, kind, sc)) continue;
+      set_splits(L, kind, sc);
+      st = launch_one(h, L, kind);
+      if (!st && cudaEventRecord(e0, h->stream) != cudaSuccess) st = TN_ECUDA;
+      for (int r = 0; r < reps && !st; ++r) st = launch_one(h, L, kind);
+      if (!st && cudaEventRecord(e1, h->stream) != cudaSuccess) st = TN_ECUDA;
+      if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = TN_ECUDA;
+      float ms = 0.f;
+      if (!st && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = TN_ECUDA;
+      if (st) break;
+      if (sc == now) now_ms = ms;
+      if (fastest == 0 || ms < fastest_ms) { fastest = sc; fastest_ms = ms; }
+    }
+    if (st) { set_splits(L, kind, now); break; }
+    float best_ms = now_ms;
+    if (fastest > 0 && (now_ms < 0.f || fastest_ms < 0.97f * now_ms)) {
+      best = fastest;
+      best_ms = fastest_ms;
+    }
+    set_splits(L, kind, best);
+    char line[64];
+    snprintf(line, sizeof(line), " %d %.3f\n", best, 1e3 * best_ms / reps);
+    table += tune_key(L, kind) + line;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->prof_on = prof;
+  cudaGetLastError();
+  if (st) return st;
+  // the loop graph is captured again with the new counts
+  if (h->loop_exec) { cudaGraphExecDestroy(h->loop_exec); h->loop_exec = nullptr; }
+  if (table_len) *table_len = table.size();
+  if (table_out && table_cap > 0) {
+    const size_t n = std::min(table.size(), table_cap - 1);
+    memcpy(table_out, table.data(), n);
+    table_out[n] = 0;
+  }
+  return TN_OK;
+}
+
+tn_status tn_autotune_apply(tn_handle* h, const char* table, int32_t* n_applied) {
+  if (!h || !table) { set_error("null argument"); return TN_EINVAL; }
+  std::vector<std::pair<std::string, int>> rows;
+  const char* p = table;
+  while (*p) {
+    const char* q = strchr(p, '\n');
+    std::string line = q ? std::string(p, q) : std::string(p);
+    p = q ? q + 1 : p + line.size();
+    char kind[16];
+    int m, n, outer, inner, prec, splits;
+    long long k;
+    double us;
+    if (sscanf(line.c_str(), "%15s %d %d %lld %d %d %d %d %lf", kind, &m, &n, &k, &outer, &inner,
+               &prec, &splits, &us) < 8)
+      continue;
+    char key[160];
+    snprintf(key, sizeof(key), "%s %d %d %lld %d %d %d", kind, m, n, k, outer, inner, prec);
+    rows.push_back({key, splits});
+  }
+  int applied = 0;
+  for (size_t li = 0; li < h->sweep.L.size(); ++li) {
+    HostLaunch& L = h->sweep.L[li];
+    const int kind = tune_kind(h, L);
+    if (kind == TUNE_NONE || (h->sweep_split > 0 && li >= h->sweep_split)) continue;
+    const std::string key = tune_key(L, kind);
+    for (auto& r : rows)
+      if (r.first == key && splits_valid(h, L, kind, r.second)) {
+        set_splits(L, kind, r.second);
+        ++applied;
+        break;
+      }
+  }
+  if (h->loop_exec) { cudaGraphExecDestroy(h->loop_exec); h->loop_exec = nullptr; }
+  if (n_applied) *n_applied = applied;
+  return TN_OK;
 }
 
 tn_status tn_bp_components(tn_handle* h, int32_t* comp_of_vertex, int32_t* sweeps_out,

@@ -2,6 +2,7 @@
 // that carries every contraction of the message and gate updates in the
 // TN_FP32 mode, the physical-leg gate, message normalisation with the FP64
 // residual, the single-site reduced density matrix and a batched block copy.
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -180,22 +181,24 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d, float* part
 // CTAs: a few sites with a long contraction, e.g. the closes) is split into at
 // most 64 pieces of at least 256 K values, each summed with the compensated
 // slices, the pieces then summed in FP64 in a fixed order by the reduce.
-int cgemm_plan(const GemmDesc& d, size_t* part_floats) {
+int cgemm_plan(const GemmDesc& d, size_t* part_floats, int force_splits) {
   const int64_t K = (int64_t)d.K1 * d.K2;
   const int64_t ctas = (int64_t)((d.N + BN - 1) / BN) * ((d.M + BM - 1) / BM) * d.n_outer * d.n_inner;
   int s = 1;
-  if (ctas < 152)
+  if (force_splits > 0)
+    s = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)force_splits, 64, (K + BK - 1) / BK}));
+  else if (ctas < 152)
     while (s < 64 && ctas * s * 2 <= 2 * 152 && K / (2 * s) >= 256) s *= 2;
   *part_floats = s > 1 ? (size_t)s * d.n_outer * d.n_inner * 2 * d.M * d.N : 0;
   return s;
 }
 
 cudaError_t launch_cgemm(const GemmDesc& d, cudaStream_t s, float* part, size_t part_cap,
-                         int* n_kernels) {
+                         int* n_kernels, int force_splits) {
   if (n_kernels) *n_kernels = 0;
   if (d.M <= 0 || d.N <= 0 || d.n_outer <= 0 || d.n_inner <= 0) return cudaSuccess;
   size_t pf = 0;
-  int splits = part ? cgemm_plan(d, &pf) : 1;
+  int splits = part ? cgemm_plan(d, &pf, force_splits) : 1;
   if (splits > 1 && pf > part_cap) splits = 1;  // the caller's partial buffer is too small
   const int K = d.K1 * d.K2;
   const int kps = splits > 1 ? ((K + splits - 1) / splits + BK - 1) / BK * BK : K;

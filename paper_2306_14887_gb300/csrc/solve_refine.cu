@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1) refine_kernel(SolveArgs a, int cw
 // then D_v[b][perm_b[s]][pos] = W[(b, s)] sqrt(sigma / ||sigma||) and
 // D_w[q][e][pos] = sum_b b_b(q) conj(Y[(b, pinv_b(e))]) / sqrt(sigma ||sigma||)
 // with b_b(q) = exp(s i pi/4 s_b s_q), as the gate split gives.
-__global__ void __launch_bounds__(kThreads, 1) legs_kernel(SolveArgs a, int cwmax) {
+__global__ void __launch_bounds__(kThreads, 2) legs_kernel(SolveArgs a, int cwmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int chi = a.chi, n = 2 * chi;
   cd* Ub = reinterpret_cast<cd*>(smem_raw);        // [cwmax][n] refined columns
@@ -776,11 +776,17 @@ cudaError_t launch_solve_refined_newton(const SolveArgs& a, cudaStream_t st) {
   if (sm_ref > kRefineSmemMax) return cudaErrorInvalidValue;
   refine_kernel<<<grid, kThreads, sm_ref, st>>>(a, cwmax);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // 4. FP64 leg matrices, spectrum and messages
-  const size_t sm_legs = sizeof(cd) * 2 * (size_t)cwmax * n + sizeof(double) * chi +
+  // 4. FP64 leg matrices, spectrum and messages.  The back substitution is a
+  // chain of chi dependent passes: two CTAs per SM (half the columns each)
+  // overlap their latencies.
+  int grid_l = (int)std::min<int64_t>(T, 2 * (int64_t)sm_count());
+  const int cw_fit_l = (int)((kLegsSmemMax - 8192) / (sizeof(cd) * 2 * (size_t)n));
+  grid_l = (int)std::max<int64_t>(grid_l, (T + cw_fit_l - 1) / cw_fit_l);
+  const int cw_l = (int)((T + grid_l - 1) / grid_l);
+  const size_t sm_legs = sizeof(cd) * 2 * (size_t)cw_l * n + sizeof(double) * chi +
                          sizeof(int) * 3 * chi + chi + 16;
   if (sm_legs > kLegsSmemMax) return cudaErrorInvalidValue;
-  legs_kernel<<<grid, kThreads, sm_legs, st>>>(a, cwmax);
+  legs_kernel<<<grid_l, kThreads, sm_legs, st>>>(a, cw_l);
   return cudaGetLastError();
 }
 

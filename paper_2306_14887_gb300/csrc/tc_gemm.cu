@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -614,7 +615,7 @@ cudaError_t launch_tc_reduce(const GemmDesc& d, const float* part, int splits, c
 
 // Plan a tensor-core launch for d: quad form when the contraction is long and
 // M, N small (2M <= 128), else realified-B form.
-bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {
+bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats, int force_splits) {
   const int64_t K = (int64_t)d.K1 * d.K2;
   *quad = (2 * d.M <= kTM && 2 * d.N <= kTN && !d.b_pre) ? 1 : 0;
   *splits = 1;
@@ -639,6 +640,11 @@ bool tc_plan(const GemmDesc& d, int* quad, int* splits, size_t* part_floats) {
       while (ctas * s < 2 * 152 && s * 2 <= ktiles / 4 && s < 64) s *= 2;
     *splits = s;
   }
+  if (force_splits > 0) {
+    // the autotuner's count, at most one K tile per split
+    const int64_t kt = *quad ? (K + kel - 1) / kel : (2 * K + kel - 1) / kel;
+    *splits = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)force_splits, 64, kt}));
+  }
   if (*splits > 1) *part_floats = (size_t)(*splits) * batch * 2 * d.M * d.N;
   return true;
 }
@@ -659,13 +665,13 @@ cudaError_t tc_prepare() {
 }
 
 cudaError_t launch_cgemm_tc(const GemmDesc& d, float* part, int* err, cudaStream_t st,
-                            int* n_kernels) {
+                            int* n_kernels, int force_splits, size_t part_cap) {
   if (n_kernels) *n_kernels = 0;
   if (d.M <= 0 || d.N <= 0 || d.n_outer <= 0 || d.n_inner <= 0) return cudaSuccess;
   int quad, splits;
   size_t pf;
-  if (!tc_plan(d, &quad, &splits, &pf)) return cudaErrorInvalidValue;
-  if (splits > 1 && !part) return cudaErrorInvalidValue;
+  if (!tc_plan(d, &quad, &splits, &pf, force_splits)) return cudaErrorInvalidValue;
+  if (splits > 1 && (!part || pf > part_cap)) return cudaErrorInvalidValue;
   TcArgs t;
   t.quad = quad;
   t.bf16 = (d.prec == TN_BF16 || d.prec == TN_BF16X3) ? 1 : 0;
