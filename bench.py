@@ -233,7 +233,13 @@ def serve_mix_leg(tn, args):
             gn, ge, gc = graphs[size]
             tickets.append(srv.submit(gn, ge, gc, chi, theta, steps, prec=args.prec))
         for i, t in enumerate(tickets):
-            z, info = srv.wait(t)
+            # the server records each job's latency itself, so the order of the
+            # waits does not matter; a large job may finish last under the
+            # least-work-first policy
+            res = srv.wait(t, timeout=1e7)
+            if res is None:
+                raise RuntimeError("serving job %d did not finish" % i)
+            z, info = res
             lat.append(info["latency_s"])
             steps_done += info["steps_done"]
             by_kind.setdefault("%dq" % stream[i][1], []).append(info["latency_s"])
@@ -666,6 +672,7 @@ def run_ours(args, rank, world, local):
     tma_launches = 0
     bp_iters = 0
     disc = 0.0
+    jac_sweeps = jac_edges = jac_max = 0
     for _ in range(args.steps):
         s.apply_floquet(theta, 1)
         st = s.stats()
@@ -673,6 +680,9 @@ def run_ours(args, rank, world, local):
         tma_launches += st["tma_launches"]
         bp_iters += st["bp_iters_total"]
         disc = max(disc, st["discarded_max"])
+        jac_sweeps += st["solve_sweeps"]
+        jac_edges += st["solve_edges"]
+        jac_max = max(jac_max, st["solve_sweeps_max"])
     e1.record(stream)
     stream.synchronize()
     ms = e0.elapsed_time(e1)
@@ -759,6 +769,8 @@ def run_ours(args, rank, world, local):
         "autotune": tune,
         "tma_stream_launches": int(tma_launches),
         "bp_sweeps_per_step": round(bp_iters / args.steps, 2),
+        "jacobi_sweeps_per_edge": {"mean": round(jac_sweeps / max(1, jac_edges), 2),
+                                   "max": int(jac_max)},
         "discarded_weight_max": disc,
         "roofline": rl,
         "peaks_measured": mp,
