@@ -323,17 +323,8 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
   //    (lower triangles, rounded) with their pivot orders and ranks instead.
   const int ldv = chi + 1;
   if (a.basis) {
-    const RefineLayout lay = refine_layout(chi);
-    const double* rbase = a.work + (int64_t)edge * lay.stride;
-    const int* rints = reinterpret_cast<const int*>(rbase + lay.ints);
-    const double2* L64 = reinterpret_cast<const double2*>(rbase + lay.L);
-    for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
-      const int p = idx / (chi * chi), o = idx % (chi * chi);
-      const double2 l = L64[idx];
-      s.Lv[p * chi * ldv + (o / chi) * ldv + o % chi] = make_float2((float)l.x, (float)l.y);
-    }
-    for (int i = tid; i < 2 * chi; i += blockDim.x) s.perm_v[i] = rints[i];
-    if (tid < 2) s.rank[tid] = rints[2 * chi + tid];
+    // the FP64 factors come from chol64_kernel, which may still be running
+    // (programmatic dependent launch): they are read after the G_w Cholesky
   } else {
     for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
       const int p = idx / (chi * chi), o = idx % (chi * chi);
@@ -374,6 +365,22 @@ __global__ void __launch_bounds__(kThreads) solve32_kernel(SolveArgs a) {
     const Group gall{0, kThreads, 0};
     pivoted_cholesky32(X, n, n, s.perm_w, ctol, &s.rank[2], s.red_i, s.red_v, s.dmax0 + 2, colk,
                        gall);
+  }
+  if (a.basis) {
+    // wait for chol64_kernel (all of its writes visible), then take its factors
+    cudaGridDependencySynchronize();
+    const RefineLayout lay = refine_layout(chi);
+    const double* rbase = a.work + (int64_t)edge * lay.stride;
+    const int* rints = reinterpret_cast<const int*>(rbase + lay.ints);
+    const double2* L64 = reinterpret_cast<const double2*>(rbase + lay.L);
+    for (int idx = tid; idx < 2 * chi * chi; idx += blockDim.x) {
+      const int p = idx / (chi * chi), o = idx % (chi * chi);
+      const double2 l = L64[idx];
+      s.Lv[p * chi * ldv + (o / chi) * ldv + o % chi] = make_float2((float)l.x, (float)l.y);
+    }
+    for (int i = tid; i < 2 * chi; i += blockDim.x) s.perm_v[i] = rints[i];
+    if (tid < 2) s.rank[tid] = rints[2 * chi + tid];
+    __syncthreads();
   }
 
   // 2. K^T = R_w R_v^T.  First X <- conj(L_w^T) so that row j of X holds
@@ -1093,8 +1100,23 @@ cudaError_t launch_solve32(const SolveArgs& a, cudaStream_t st) {
   });
   if (attr != cudaSuccess) return attr;
   const size_t sm = smem_bytes(a.chi);
-  solve32_kernel<<<a.n_edges, kThreads, sm, st>>>(a);
-  return cudaGetLastError();
+  if (!a.basis) {
+    solve32_kernel<<<a.n_edges, kThreads, sm, st>>>(a);
+    return cudaGetLastError();
+  }
+  // basis mode follows chol64_kernel on the same stream: a programmatic
+  // dependent launch, so that the G_w Cholesky runs while chol64 finishes
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.n_edges);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr_pdl[1];
+  attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr_pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr_pdl;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, solve32_kernel, a);
 }
 
 }  // namespace tnbp

@@ -205,6 +205,9 @@ __global__ void __launch_bounds__(kThreads) chol64_kernel(SolveArgs a) {
   int* ints = reinterpret_cast<int*>(base + lay.ints);
   // the factorisation runs in shared memory (padded rows) up to kSmemChi and in
   // place in the edge's L block of the workspace above
+  // the basis kernel that follows may start (its first phase does not read
+  // these factors; it waits for this grid before it does)
+  cudaTriggerProgrammaticLaunchCompletion();
   const bool in_smem = chi <= kSmemChi;
   const int ld = in_smem ? chi + 1 : chi;
   cd* A = in_smem ? reinterpret_cast<cd*>(smem_raw)
