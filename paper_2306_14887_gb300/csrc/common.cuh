@@ -56,7 +56,17 @@ struct GemmDesc {
   // [2N][2K] row-major matrix Bt[(t,n)][(s,k)] = [[B_re, B_im], [-B_im, B_re]][s][t]
   // (the fields b_n, b_k2, plane_b then describe its complex view).
   int32_t b_pre;
+  // BP sweep launches over a disjoint union: the component of each outer
+  // entry and the stop rule's per-component state; a CTA whose component has
+  // stopped returns at once (null: no skipping).  Honoured by the tile GEMM,
+  // the CUDA-core GEMM and the split-K reduce.
+  const int* outer_comp;
+  const double* comp_state;
 };
+// true when the outer entry's component has met the BP stop rule
+__device__ __forceinline__ bool outer_frozen(const GemmDesc& d, int outer) {
+  return d.outer_comp && d.comp_state[4 * d.outer_comp[outer] + 3] != 0.0;
+}
 
 // Row offset for the two- or three-level row index: with M3 > 1,
 // m = (m1 * M2 + m2) * M3 + m3 and the offset is m1*s1 + m2*s2 + m3*s3; with

@@ -44,13 +44,14 @@ int64_t ipow(int64_t b, int e) {
 }
 
 struct HostLaunch {
-  GemmDesc d;
+  GemmDesc d{};
   std::vector<const float*> A, B;
   std::vector<float*> C;
   TcStreamPlan sp;         // maps set: the launch runs in a TMA kernel
   bool fuse_next = false;  // the next launch contracts this one's output (chain stages)
   bool skip = false;       // carried out by the previous launch's fused kernel
   int tuned = 0;           // split-K count chosen by tn_autotune (0: the heuristic)
+  std::vector<int> outer_site;  // sweep launches: the site of each outer entry
 };
 
 struct Plan {
@@ -727,25 +728,57 @@ void build_sweep_plan(tn_handle* h) {
   // All sites of a degree in one launch per chain stage: grouping the sites so
   // that a group's intermediates stay in L2 costs more in lost parallelism
   // than it saves in traffic (measured at chi = 64 on 127 qubits).
+  // every launch's outer entries are the sites of one degree, in list order
+  auto tag = [&](size_t from, const std::vector<int>& sites) {
+    for (size_t i = from; i < P.L.size(); ++i) P.L[i].outer_site = sites;
+  };
   const std::vector<int>& s3 = h->sites_by_deg[3];
   for (int which = 0; which < 3; ++which) {
     std::vector<float*> outs;
     for (int v : s3) outs.push_back((float*)msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][which])));
+    const size_t from = P.L.size();
     deg3_chain(h, P, which, s3, false, outs);
+    tag(from, s3);
   }
   h->sweep_split = P.L.size();
   const std::vector<int>& s2 = h->sites_by_deg[2];
   for (int which = 0; which < 2; ++which) {
     std::vector<float*> outs;
     for (int v : s2) outs.push_back((float*)msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][which])));
+    const size_t from = P.L.size();
     deg2_chain(h, P, which, s2, false, outs);
+    tag(from, s2);
   }
   std::vector<Ent> d1;
   for (int v : h->sites_by_deg[1]) {
     const float* T = site_ptr(h, h->T, v);
     d1.push_back({T, T, msg_ptr(h, h->raw, dir_id(g, v, g.legs[v][0]))});
   }
+  const size_t from = P.L.size();
   add_close(P, 1, 0, h->chi, false, h->cfg.prec, d1);
+  tag(from, h->sites_by_deg[1]);
+}
+
+// A union of several components: every sweep launch gets the component of
+// each of its outer entries, so that the kernels that honour it skip the
+// components that have met the stop rule.
+tn_status attach_components(tn_handle* h) {
+  if (h->n_comp <= 1) return TN_OK;
+  for (auto& L : h->sweep.L) {
+    if (L.outer_site.empty() || (int)L.outer_site.size() != L.d.n_outer) continue;
+    std::vector<int> comp(L.outer_site.size());
+    for (size_t i = 0; i < comp.size(); ++i) comp[i] = h->comp_of_vertex[L.outer_site[i]];
+    int* dc = (int*)dev_alloc(h, sizeof(int) * comp.size());
+    if (!dc) { set_error("device allocation of the component tables failed"); return TN_ENOMEM; }
+    if (cudaMemcpy(dc, comp.data(), sizeof(int) * comp.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      set_error("upload of the component tables failed");
+      return TN_ECUDA;
+    }
+    L.d.outer_comp = dc;
+    L.d.comp_state = h->comp_state;
+  }
+  return TN_OK;
 }
 
 // Environments of both sides of every edge in layer `li`, open p, into gram;
@@ -1697,6 +1730,8 @@ tn_status tn_create(const tn_graph* graph, const tn_config* cfg, const tn_alloca
   }
   tn_status st = upload_plans(h);
   if (st) { delete[] h->h_stats; return fail(st); }
+  st = attach_components(h);
+  if (st) { delete[] h->h_stats; return fail(st); }
   st = init_state(h);
   if (st) { delete[] h->h_stats; return fail(st); }
   *out = h;
@@ -1814,6 +1849,13 @@ tn_status tn_autotune(tn_handle* h, int32_t reps, char* table_out, size_t table_
   if (st) return st;
   st = ensure_mrt(h);
   if (st) return st;
+  // the launches skip components the last BP iteration marked stopped: clear
+  // the marks while timing, and put the state back afterwards
+  std::vector<double> comp_saved(4 * (size_t)std::max(1, h->n_comp));
+  TN_CUDA_TRY(cudaMemcpyAsync(comp_saved.data(), h->comp_state, sizeof(double) * comp_saved.size(),
+                              cudaMemcpyDeviceToHost, h->stream));
+  TN_CUDA_TRY(launch_bp_loop_init(h->n_comp, h->comp_state, h->comp_res, h->res_bits, h->loop_par,
+                                  1e-10, 1, 1.0, h->loop_out, h->stream));
   TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
   const bool prof = h->prof_on;
   h->prof_on = false;
@@ -1868,6 +1910,9 @@ tn_status tn_autotune(tn_handle* h, int32_t reps, char* table_out, size_t table_
   cudaEventDestroy(e1);
   h->prof_on = prof;
   cudaGetLastError();
+  TN_CUDA_TRY(cudaMemcpyAsync(h->comp_state, comp_saved.data(), sizeof(double) * comp_saved.size(),
+                              cudaMemcpyHostToDevice, h->stream));
+  TN_CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (st) return st;
   // the loop graph is captured again with the new counts
   if (h->loop_exec) { cudaGraphExecDestroy(h->loop_exec); h->loop_exec = nullptr; }

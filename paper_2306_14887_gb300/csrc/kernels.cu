@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(GemmDesc d, float* part
   z /= splits;
   const int outer = z / d.n_inner;
   const int inner = z - outer * d.n_inner;
+  if (outer_frozen(d, outer)) return;  // a converged component of a union
   const float* A = d.A[outer] + inner * d.a_in;
   const float* B = d.B[outer] + inner * d.b_in;
   float* C = d.C[outer] + inner * d.c_in;

@@ -165,6 +165,9 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
   const int split = z % t.splits;
   z /= t.splits;
   const int outer = z / d.n_inner, inner = z - (z / d.n_inner) * d.n_inner;
+  // a converged component of a union: nothing is initialised yet, the whole
+  // CTA leaves together
+  if (outer_frozen(d, outer)) return;
   const float* A = d.A[outer] + inner * d.a_in;
   const float* B = d.B[outer] + inner * d.b_in;
   const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * t.tn;
@@ -584,6 +587,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(GemmDesc d, TcArgs
 __global__ void tc_reduce_kernel(GemmDesc d, const float* part, int splits) {
   const int z = blockIdx.y;
   const int outer = z / d.n_inner, inner = z - outer * d.n_inner;
+  if (outer_frozen(d, outer)) return;
   const int M = d.M, N = d.N;
   float* C = d.C[outer] + inner * d.c_in;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < M * N; idx += gridDim.x * blockDim.x) {
