@@ -324,6 +324,9 @@ __global__ void __launch_bounds__(kCThreads, 2) tc_close_kernel(GemmDesc d, Clos
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int e = blockIdx.y, split = blockIdx.x;
+  // a converged component of a union: nothing is initialised yet, the whole
+  // CTA leaves together (its partial is never read: the reduce skips it too)
+  if (outer_frozen(d, e / d.n_inner)) return;
   const int c0 = split * a.per_split;
   const int c1 = min(a.chunks, c0 + a.per_split);
   const int nt = c1 > c0 ? c1 - c0 : 0;  // >= 1 by the host's choice of splits
