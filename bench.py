@@ -310,6 +310,12 @@ def batch_run(tn, args, prec):
         b.evolve(1)
     torch.cuda.synchronize()
     with tn.Batch(insts, prec=prec, solve=args.solve) as b:
+        tuned = None
+        if not args.no_autotune:
+            # split-K counts per (chi, degree) launch shape, on the initial states (untimed)
+            tables = b.autotune(reps=3)
+            tuned = {str(chi): sum(1 for ln in t.splitlines() if ln.strip())
+                     for chi, t in tables.items()}
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b.evolve(steps)
@@ -347,6 +353,7 @@ def batch_run(tn, args, prec):
             "dz_vs_oracle": [None if d is None else float("%.3g" % d) for d in d_oracle],
             "oracle_near_ties": near_tie,
             "bp_sweeps_last": [int(x) for x in sweeps],
+            "autotuned_rows_by_chi": tuned,
             "prec": prec,
             "note": "oracle values from tests/golden/batched64_oracle.txt (FP64 oracle on every "
                     "instance with chi <= 16, chi = 32 up to 127 qubits, chi = 64 at 27 qubits)"}

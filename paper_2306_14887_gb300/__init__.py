@@ -591,6 +591,11 @@ class Batch:
         if errs:
             raise errs[0]
 
+    def autotune(self, reps=3):
+        """Split-K autotuning (tn_autotune) of every group's union handle on
+        its current state; returns {chi: table}."""
+        return {g[0]: g[4].autotune(reps) for g in self.groups}
+
     def expect_z(self):
         """<Z_v> of every instance, in input order."""
         out = [None] * len(self.sizes)

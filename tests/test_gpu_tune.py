@@ -81,3 +81,20 @@ def test_table_applies_to_another_handle(tnlib, tmp_path):
     # another chi: no key matches
     with tnlib.TNState(g.n, g.edges, g.colours, chi=16, prec="tf32") as d:
         assert d.apply_tuning(table) == 0
+
+
+def test_batch_autotune_keeps_results(tnlib):
+    """A union handle tuned on its initial state evolves to the untuned result
+    up to the order of the FP32 partial sums."""
+    gs = [OG.falcon27_patch(), OG.eagle127(), OG.heavy_hex(5, 11)]
+    insts = [(g.n, g.edges, g.colours, 8, th) for g, th in zip(gs, (0.4, 0.9, 1.2))]
+    out = []
+    for tune in (False, True):
+        with tnlib.Batch(insts, prec="fp32") as b:
+            if tune:
+                tables = b.autotune(reps=2)
+                assert set(tables) == {8}
+            b.evolve(4)
+            out.append(b.expect_z())
+    for za, zb in zip(*out):
+        assert np.abs(za - zb).max() < 2e-6
