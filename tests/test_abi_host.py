@@ -146,6 +146,20 @@ def test_server_rejects_bad_config_before_touching_a_device():
     cfg.max_slots = 0
     h = tn.C.c_void_p()
     assert tn.lib().tn_server_create(tn.C.byref(cfg), tn.C.byref(h)) == -1
+    # an admission policy other than TN_SERVE_FIFO (0) and TN_SERVE_SHORTEST (1)
+    cfg.max_slots = 2
+    cfg.policy = 7
+    assert tn.lib().tn_server_create(tn.C.byref(cfg), tn.C.byref(h)) == -1
+    assert not h.value
+
+
+def test_autotune_and_components_reject_null_handles():
+    L = tn.lib()
+    n = tn.C.c_size_t()
+    assert L.tn_autotune(None, 3, None, 0, tn.C.byref(n)) == -1
+    assert L.tn_autotune_apply(None, b"", None) == -1
+    nc = tn.C.c_int32()
+    assert L.tn_bp_components(None, None, None, None, 0, tn.C.byref(nc)) == -1
 
 
 def test_chi_extrapolation_matches_least_squares():
