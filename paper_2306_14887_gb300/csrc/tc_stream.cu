@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
       const uint32_t bbytes = (uint32_t)(a.kc * a.nr * 128);
       for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile) {
         const int e = tile / a.tiles_per_entry;
+        if (outer_frozen(d, e)) continue;  // every role skips the same tiles
         const int mt = tile - e * a.tiles_per_entry;
         if (e != cur) {
           if (cur >= 0 && !mbar_wait(bempty, (bl - 1) & 1, a.err)) { *abort_flag = 1; break; }
@@ -204,9 +205,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
     // ------------------------------------------------------------ MMA issue
     if (lane == 0) {
       const uint32_t idesc = make_idesc(2, 128, a.nr);
-      int it = 0, cur = -1, bl = 0, i = 0;
-      for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile, ++i) {
+      int it = 0, cur = -1, bl = 0, i = 0;  // i: tiles processed (the skipped ones not counted)
+      for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile) {
         const int e = tile / a.tiles_per_entry;
+        if (outer_frozen(d, e)) continue;
         if (e != cur) {
           if (cur >= 0) mma_commit(bempty);  // arrives once the MMAs reading Bt are done
           if (!mbar_wait(bfull, bl & 1, a.err)) { *abort_flag = 1; break; }
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
         }
         if (!ok) { *abort_flag = 1; break; }
         mma_commit(&tfull[acc]);
+        ++i;
       }
       // all MMAs issued by this thread complete before TMEM is freed
       mma_commit(done);
@@ -244,10 +247,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
     // ------------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const int row = q * 32 + lane;
-    int i = 0;
-    for (int tile = t_beg; tile < t_end; ++tile, ++i) {
+    int i = 0;  // tiles processed (the skipped ones not counted)
+    for (int tile = t_beg; tile < t_end; ++tile) {
       if (*abort_flag) break;
       const int e = tile / a.tiles_per_entry;
+      if (outer_frozen(d, e)) continue;
       const int mt = tile - e * a.tiles_per_entry;
       const int acc = i & 1;
       const bool ok = mbar_wait(&tfull[acc], (i >> 1) & 1, a.err);
@@ -275,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stream_kernel(GemmDesc d, Stre
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[acc]);
+      ++i;
     }
   }
 
@@ -557,6 +562,7 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
       const uint32_t bbytes = (uint32_t)(2 * 3 * KCS * CHI * 128);
       for (int tile = t_beg; tile < t_end && !*abort_flag; ++tile) {
         const int e = tile / a.tiles_per_entry;
+        if (outer_frozen(d, e)) continue;  // every role skips the same tiles
         const int mt = tile - e * a.tiles_per_entry;
         if (e != cur) {
           if (cur >= 0 && !mbar_wait(bempty, (bl - 1) & 1, a.err)) { *abort_flag = 1; break; }
@@ -649,10 +655,11 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
           __nanosleep(20);
         }
       };
-      int it = 0, cur = -1, bl = 0, i = 0;
+      int it = 0, cur = -1, bl = 0, i = 0;  // i: tiles processed (the skipped ones not counted)
       bool ok = true;
-      for (int tile = t_beg; tile < t_end && ok && !*abort_flag; ++tile, ++i) {
+      for (int tile = t_beg; tile < t_end && ok && !*abort_flag; ++tile) {
         const int e = tile / a.tiles_per_entry;
+        if (outer_frozen(d, e)) continue;
         if (e != cur) {
           // stage 2 of the last tile of the previous entry reads its Bt2
           if (!flush2()) { ok = false; break; }
@@ -686,6 +693,7 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
         // at most one stage 2 outstanding: the previous tile's goes first
         if (!flush2()) { ok = false; break; }
         pend = i;
+        ++i;
       }
       if (ok && !*abort_flag) ok = flush2();
       if (!ok) *abort_flag = 1;
@@ -707,10 +715,11 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
     uint32_t uoff[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) uoff[u] = (uint32_t)((((lane >> 2) ^ u)) << 4);
-    int i = 0;
-    for (int tile = t_beg; tile < t_end; ++tile, ++i) {
+    int i = 0;  // tiles processed (the skipped ones not counted)
+    for (int tile = t_beg; tile < t_end; ++tile) {
       if (*abort_flag) break;
       const int e = tile / a.tiles_per_entry;
+      if (outer_frozen(d, e)) continue;
       const int mt = tile - e * a.tiles_per_entry;
       const int buf = i & 1;
       if (!mbar_wait(&t1full[buf], (i >> 1) & 1, a.err)) { *abort_flag = 1; break; }
@@ -746,6 +755,7 @@ __global__ void __launch_bounds__(kFThreads, 1) tc_chain_kernel(GemmDesc d, Fuse
       }
       tc_fence_before();
       __syncwarp();
+      ++i;
     }
   }
 

@@ -200,3 +200,26 @@ def test_batched64_matches_oracle_golden(tnlib):
             errs.append(err)
     assert len(errs) >= len(idx) // 2
     assert np.median(errs) < 1e-6
+
+
+@pytest.mark.parametrize("chi", [32, 64])
+def test_tf32_union_with_stopped_instance_matches_alone(tnlib, chi):
+    """TF32 at chi = 32 / 64 runs the TMA kernels (streaming mode products,
+    fused chains, split-K closes), which skip the tiles of an instance once it
+    has stopped.  An instance at theta = 0 stops after its first sweeps while
+    its batch-mate continues; the batch-mate's result is the one it has alone
+    (up to the order of FP32 sums) and the stopped instance stays exactly at
+    <Z> = 1."""
+    g = OG.eagle127()
+    n, edges, cols, offs = tnlib.batch_union([(g.n, g.edges, g.colours)] * 2)
+    thetas = np.concatenate([np.zeros(g.n), np.full(g.n, 0.9)])
+    with tnlib.TNState(n, edges, cols, chi=chi, prec="tf32") as s:
+        s.apply_floquet_field(thetas, 4)
+        _, sweeps, _ = s.bp_components()
+        z = s.expect_z_all()
+    assert sweeps[0] < sweeps[1]
+    assert np.abs(z[:g.n] - 1.0).max() < 1e-5
+    with tnlib.TNState(g.n, g.edges, g.colours, chi=chi, prec="tf32") as a:
+        a.apply_floquet(0.9, 4)
+        # exact regime (chi >= 2^4): TF32 rounding alone separates the runs
+        assert np.abs(a.expect_z_all() - z[g.n:]).max() < 1e-3
