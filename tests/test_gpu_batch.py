@@ -207,9 +207,10 @@ def test_tf32_union_with_stopped_instance_matches_alone(tnlib, chi):
     """TF32 at chi = 32 / 64 runs the TMA kernels (streaming mode products,
     fused chains, split-K closes), which skip the tiles of an instance once it
     has stopped.  An instance at theta = 0 stops after its first sweeps while
-    its batch-mate continues; the batch-mate's result is the one it has alone
-    (up to the order of FP32 sums) and the stopped instance stays exactly at
-    <Z> = 1."""
+    its batch-mate continues; the stopped instance stays exactly at <Z> = 1 and
+    the batch-mate, like its alone run, is within the TF32 bound (5e-3) of the
+    exact values (chi >= 2^4: the FP64 oracle at chi = 16 is exact here).  Two
+    TF32 runs whose FP32 sums are split differently differ by up to about 2e-3."""
     g = OG.eagle127()
     n, edges, cols, offs = tnlib.batch_union([(g.n, g.edges, g.colours)] * 2)
     thetas = np.concatenate([np.zeros(g.n), np.full(g.n, 0.9)])
@@ -219,7 +220,10 @@ def test_tf32_union_with_stopped_instance_matches_alone(tnlib, chi):
         z = s.expect_z_all()
     assert sweeps[0] < sweeps[1]
     assert np.abs(z[:g.n] - 1.0).max() < 1e-5
+    exact = OB.run(g, 16, 0.9, 4).all_z()
+    assert np.abs(z[g.n:] - exact).max() < 5e-3
     with tnlib.TNState(g.n, g.edges, g.colours, chi=chi, prec="tf32") as a:
         a.apply_floquet(0.9, 4)
-        # exact regime (chi >= 2^4): TF32 rounding alone separates the runs
-        assert np.abs(a.expect_z_all() - z[g.n:]).max() < 1e-3
+        za = a.expect_z_all()
+    assert np.abs(za - exact).max() < 5e-3
+    assert np.abs(za - z[g.n:]).max() < 5e-3
