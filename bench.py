@@ -236,7 +236,7 @@ def serve_mix_leg(tn, args):
             # the server records each job's latency itself, so the order of the
             # waits does not matter; a large job may finish last under the
             # least-work-first policy
-            res = srv.wait(t, timeout=1e7)
+            res = srv.wait(t, timeout=None)
             if res is None:
                 raise RuntimeError("serving job %d did not finish" % i)
             z, info = res

@@ -554,7 +554,8 @@ tn_status tn_server_submit(tn_server* s, const tn_job* job, uint64_t* ticket);
  * job's status, with z (caller-owned, n_vertices doubles, may be NULL) and info
  * (may be NULL) filled; the ticket is then released.  TN_EINVAL: unknown ticket. */
 tn_status tn_server_poll(tn_server* s, uint64_t ticket, double* z, tn_result* info);
-/* tn_server_wait — tn_server_poll after waiting up to timeout_s seconds. */
+/* tn_server_wait — tn_server_poll after waiting up to timeout_s seconds
+ * (timeout_s <= 0: do not wait; values above 1e9 count as 1e9). */
 tn_status tn_server_wait(tn_server* s, uint64_t ticket, double timeout_s, double* z,
                          tn_result* info);
 /* tn_server_poll_ex / tn_server_wait_ex — as tn_server_poll / tn_server_wait,

@@ -698,6 +698,13 @@ class Server:
         return self._take(lib().tn_server_poll_ex, ticket)
 
     def wait(self, ticket, timeout=600.0):
+        """(<Z_v>, info) once the job ends; None if it has not ended after
+        `timeout` seconds (None: wait without a limit)."""
+        if timeout is None:
+            while True:
+                r = self._take(lib().tn_server_wait_ex, ticket, C.c_double(3600.0))
+                if r is not None:
+                    return r
         return self._take(lib().tn_server_wait_ex, ticket, C.c_double(timeout))
 
     def stats(self):

@@ -14,6 +14,7 @@
 // destroys the handle.  Jobs never share device memory or streams, and every
 // kernel of the library is deterministic (fixed reduction orders), so a job's
 // result is the same whether it runs alone or in a mix.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -312,8 +313,10 @@ tn_status tn_server_wait_ex(tn_server* s, uint64_t ticket, double timeout_s, dou
   auto it = s->jobs.find(ticket);
   if (it == s->jobs.end()) return TN_EINVAL;
   std::shared_ptr<Job> j = it->second;
+  // at most about 30 years ahead, so that the deadline fits the clock's range
+  const double wait_s = timeout_s > 0 ? std::min(timeout_s, 1e9) : 0.0;
   const auto limit = Clock::now() + std::chrono::duration_cast<Clock::duration>(
-                                        std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0));
+                                        std::chrono::duration<double>(wait_s));
   while (j->status == TN_EAGAIN) {
     if (timeout_s <= 0 || s->cv.wait_until(lk, limit) == std::cv_status::timeout) {
       if (j->status == TN_EAGAIN) return TN_EAGAIN;
